@@ -1,0 +1,70 @@
+"""The simple iteration with the S[ACG] preconditioner (Sects. 4.5-4.6) and the frame
+rotator applied after each iteration (Sect. 6.1.6), FP64."""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import blocks as B
+
+
+@dataclass
+class State:
+    src: np.ndarray   # [n_src, 5]
+    att: np.ndarray   # [n_coef, 4]
+    cal: np.ndarray   # [n_cal]
+
+    def copy(self):
+        return State(self.src.copy(), self.att.copy(), self.cal.copy())
+
+
+@dataclass
+class IterStats:
+    chi2: float            # sum_l W_l R_l^2 after the source update
+    Q: float               # sum_i Q_i
+    nu: int                # sum_i nu_i
+    n_out: int
+    rank_def_s: int
+    rank_def_a: int
+    rank_def_c: int
+    frame: np.ndarray      # (eps, omega) applied, 6 values
+    d_rms: np.ndarray      # RMS of the 5 source updates (rad, rad/yr)
+
+
+def iterate_once(P, state, st, ref=None):
+    """One AGIS iteration in the order of Sect. 4.6: s^(k+1) from a^(k), c^(k); then a^(k+1)
+    and c^(k+1) both from s^(k+1) with the old a^(k), c^(k); then the frame rotator."""
+    src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st)
+    att1, rda = state.att.copy(), 0
+    cal1, rdc = state.cal.copy(), 0
+    if "A" in st.block_mask:
+        att1, rda = B.attitude_update(P, state.att, ev, sres.R, sres.W, st)
+    if "C" in st.block_mask:
+        cal1, rdc = B.calibration_update(P, state.cal, ev, sres.R, sres.W)
+    frame = np.zeros(6)
+    if st.frame_each_iter and ref is not None:
+        eps, om = B.frame_fit(P, src1, ref)
+        src1 = B.frame_apply_sources(P, src1, eps, om)
+        att1 = B.frame_apply_attitude(P, att1, eps, om)
+        frame = np.concatenate([eps, om])
+    stats = IterStats(
+        chi2=float(np.sum(sres.W * sres.R ** 2)), Q=float(np.sum(sres.Qi)), nu=int(np.sum(sres.nu)),
+        n_out=int(np.sum(sres.n_out)), rank_def_s=int(np.sum(sres.rank_def)), rank_def_a=int(rda),
+        rank_def_c=int(rdc), frame=frame, d_rms=np.sqrt(np.mean(sres.d ** 2, axis=0)))
+    return State(src1, att1, cal1), stats, sres
+
+
+def iterate(P, state, st, n_iter, ref=None, callback=None):
+    hist = []
+    for k in range(n_iter):
+        state, stats, _ = iterate_once(P, state, st, ref)
+        hist.append(stats)
+        if callback is not None:
+            callback(k, state, stats)
+    return state, hist
+
+
+def source_errors(src, truth):
+    """Per-parameter errors of the sources (alpha* as a true arc)."""
+    e = np.asarray(src) - np.asarray(truth)
+    e[:, 0] = (np.mod(e[:, 0] + np.pi, 2 * np.pi) - np.pi) * np.cos(np.asarray(truth)[:, 1])
+    return e
