@@ -1,0 +1,312 @@
+"""Benchmark of the AGIS hot path on GB300: AL+AC observations per second per AGIS iteration.
+
+One step = one S[ACG] iteration (S pass and 5x5 solves, A pass and segmented banded
+Cholesky, C pass and constraint projection, frame rotator) over the whole synthetic
+workload, replayed as one CUDA graph.  Inputs are resident in HBM for `value`; `e2e`
+repeats the measurement through the C ABI from host buffers (upload, set-up, one
+iteration, read-back of the updated sources).  `--impl reference` times the FP64 oracle
+on the host cores on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+For N > 1 (launched with torch.distributed.run) every rank runs an independent replica:
+the iteration couples all sources through the attitude, and this library runs on one GPU.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "scale5yr": "1M sources, 5 yr, 30-s knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
+    "small1yr": "10k sources, 1 yr, 1-h knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
+}
+# kernels launched by one iteration: S (source update, stats), A (accumulate, assemble,
+# solve, apply, rank-defect sum), C (accumulate, project, rank-defect sum), frame (normals,
+# solve, apply sources, apply attitude)
+KERNELS_PER_STEP = 14
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="scale5yr", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--n-src", type=int, default=0, help="override the number of sources (testing)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# Algorithmic FP64 operations per observation of the S pass ("Roofline"):
+# forward model 160, partials 60, robust sigma 10, 5 normal-equation passes x 26 and
+# 5 residual passes x 12, hand-over 10.  Transcendentals (sincos, atan2, sqrt, exp, div)
+# count as one operation each.
+S_FLOPS_PER_OBS = 160 + 60 + 10 + 5 * 26 + 5 * 12 + 10
+
+
+def cpu_baseline(ds, seconds=15.0):
+    """The FP64 oracle on a bounded sample of the workload, scaled to observations/s per
+    iteration: S block on a sample of sources, A block on one segment (all observations of
+    its time range), C block on one calibration interval."""
+    import oracle.blocks as OB
+    import oracle.model as OM
+    P = OM.problem_from_dataset(ds)
+    st = OB.Settings(seg_len=2880 if ds.geometry["knot_dt_ns"] == 30_000_000_000 else 720, seg_overlap=12)
+    rng = np.random.default_rng(0)
+    # --- S: sources until ~1/2 of the budget
+    order = rng.permutation(ds.n_src)
+    t0 = time.perf_counter()
+    n_obs_s = 0
+    n_done = 0
+    while time.perf_counter() - t0 < 0.5 * seconds and n_done < ds.n_src:
+        idx = np.sort(order[n_done:n_done + 50])
+        sub = ds.subset_sources(idx)
+        Ps = OM.problem_from_dataset(sub)
+        OB.source_update(Ps, sub.src0, sub.att0, sub.cal0, st)
+        n_obs_s += sub.n_obs
+        n_done += idx.size
+    t_s = (time.perf_counter() - t0) / max(1, n_obs_s)
+    # --- A: one segment in the middle of the mission, with every observation of its range
+    segs = OB.segments(P, st)
+    l_lo, l_hi, n_lo, n_hi, u_lo, u_hi = segs[len(segs) // 2]
+    kn = P.knots()
+    sel = np.nonzero((ds.t_ns >= kn[l_lo]) & (ds.t_ns < kn[l_hi + 1]))[0]
+    t1 = time.perf_counter()
+    ev = OM.evaluate(P, ds.src0, ds.att0, ds.cal0, idx=sel)
+    W = 1.0 / ds.sigma[sel].astype(np.float64) ** 2
+    evf = {k: v for k, v in ev.items()}
+    evf["l"] = ev["l"]
+    Nb, b = OB.attitude_normals(P, evf, ev["R"], W, st, l_lo, l_hi)
+    from oracle import cholesky as CH
+    CH.band_solve(Nb, b)
+    t_a_seg = time.perf_counter() - t1
+    # --- C: one calibration interval
+    day = ds.geometry["n_cal_days"] // 2
+    csel = np.nonzero(OM.cal_day(P, ds.t_ns) == day)[0]
+    t2 = time.perf_counter()
+    ev2 = OM.evaluate(P, ds.src0, ds.att0, ds.cal0, idx=csel, partials=False)
+    k = ev2["cal_k"]
+    np.bincount(k, weights=1.0 / ds.sigma[csel].astype(np.float64) ** 2, minlength=P.n_cal)
+    t_c_day = time.perf_counter() - t2
+    t_iter = t_s * ds.n_obs + t_a_seg * len(segs) + t_c_day * ds.geometry["n_cal_days"]
+    sample = (f"S block on {n_done} sources ({n_obs_s} obs), A block on 1 of {len(segs)} segments "
+              f"({sel.size} obs), C block on 1 of {ds.geometry['n_cal_days']} days ({csel.size} obs); "
+              f"per-iteration time extrapolated to {ds.n_obs} obs = {t_iter:.1f} s")
+    return {"value": ds.n_obs / t_iter, "unit": "obs/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def make_dataset(args):
+    import synth
+    over = {}
+    if args.n_src:
+        over["n_src"] = args.n_src
+    t = time.perf_counter()
+    ds = synth.simulate(synth.config(args.workload, **over))
+    return ds, time.perf_counter() - t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ds, _ = make_dataset(args)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(ds, seconds=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
+        if k >= args.warmup:
+            vals.append(cb)
+    v = float(np.median([c["value"] for c in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "AL+AC observations/s per AGIS iteration", "value": v, "unit": "obs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ds.n_obs / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs,
+                       "n_src": ds.n_src}, "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "obs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1112_4139_gb300 as pkg
+    pkg.build()
+    from paper_1112_4139_gb300 import agis
+    ds, t_gen = make_dataset(args)
+    stream = torch.cuda.Stream()
+    cfg = agis.default_config(seg_len=2880 if ds.geometry["knot_dt_ns"] == 30_000_000_000 else 720,
+                              use_graph=1, frame_each_iter=1)
+    # ---- device-resident inputs
+    obs_d = agis.obs_from_dataset(ds, device="cuda")
+    t = time.perf_counter()
+    g = agis.Agis(ds.geometry, cfg, obs_d, np.ascontiguousarray(ds.src0), np.ascontiguousarray(ds.att0),
+                  np.ascontiguousarray(ds.cal0), src_ref=np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]),
+                  stream=stream.cuda_stream)
+    t_init = time.perf_counter() - t
+    del obs_d
+    g.iterate(args.warmup)
+    # flush-free timing: the inputs (>= tens of GB) are far larger than the 129 MB L2
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    its = g.iterate(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * ds.n_obs / (ms * 1e-3)
+    s_ms = float(np.median([it["s"]["elapsed_ms"] for it in its]))
+    a_ms = float(np.median([it["a"]["elapsed_ms"] for it in its]))
+    g.close()
+    # ---- end to end through the C ABI from pinned host buffers
+    import torch as T
+    host = {k: T.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in agis.obs_from_dataset(ds).items()}
+    src0 = T.from_numpy(np.ascontiguousarray(ds.src0)).pin_memory()
+    att0 = T.from_numpy(np.ascontiguousarray(ds.att0)).pin_memory()
+    cal0 = T.from_numpy(np.ascontiguousarray(ds.cal0)).pin_memory()
+    ref = T.from_numpy(np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]])).pin_memory()
+    out_src = T.empty((ds.n_src, 5), dtype=T.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + sum(
+        v.numel() * v.element_size() for v in (src0, att0, cal0, ref))
+    d2h = out_src.numel() * out_src.element_size()
+    e2e_times = []
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ge = agis.Agis(ds.geometry, cfg, host, src0, att0, cal0, src_ref=ref, stream=stream.cuda_stream)
+        ge.iterate(1)
+        ge.sources(out=out_src.numpy())
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t)
+        ge.close()
+    e2e = world * ds.n_obs / float(np.median(e2e_times))
+    peaks = load_peaks()
+    # FP64 arithmetic bound: the S pass is limited by the FP64 pipe (the design doc derives the
+    # peak from the FP64 unit count and clock: 1.25 TFLOP/s nominal for GB300)
+    fp64_peak = 1.25
+    achieved = S_FLOPS_PER_OBS * ds.n_obs / (s_ms * 1e-3) / 1e12
+    line = {
+        "metric": "AL+AC observations/s per AGIS iteration", "value": value, "unit": "obs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs,
+                   "n_src": ds.n_src, "n_coef": ds.n_coef, "n_cal": ds.n_cal,
+                   "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "t_generate_s": round(t_gen, 1), "t_init_s": round(t_init, 2)},
+        "e2e": {"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "kernel": "k_source_update (S pass, FP64)", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock), not in MEASURED_PEAKS.json",
+                     "flops_per_obs": S_FLOPS_PER_OBS},
+        "block_ms": {"S": s_ms, "A": a_ms, "rest": ms - s_ms - a_ms},
+    }
+    if peaks.get("hbm_gbs"):
+        line["roofline"]["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

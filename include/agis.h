@@ -1,0 +1,189 @@
+/*
+ * agis.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot path of the
+ * Astrometric Global Iterative Solution (Lindegren et al. 2012, arXiv:1112.4139).
+ *
+ * The library owns its device memory.  Every pointer argument may be host or device
+ * memory (unified addressing); sizes are element counts.  No call throws; every call
+ * returns AGIS_OK (0) or a negative code, and agis_last_error() gives a message.
+ * One context per host thread.  Rank deficiency is reported in the statistics, never as
+ * an error (App. C.3).
+ *
+ * Units: radians, radians per Julian year (365.25 d), int64 nanoseconds of TCB since a
+ * fixed origin.  Astrometric parameters are (alpha, delta, parallax, mu_alpha*, mu_delta)
+ * with mu_r = 0 (Sect. 3.2); attitude coefficients are quaternions {x, y, z, w} of the
+ * cubic B-spline of Eq. qspline; calibration parameters are the r = 0 offsets of
+ * Eq. etazeta, indexed as described at agis_init.
+ */
+#ifndef AGIS_H
+#define AGIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AGIS_ABI_VERSION 1
+
+#define AGIS_OK 0
+#define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
+#define AGIS_E_CUDA (-2)       /* CUDA runtime error                                    */
+#define AGIS_E_OOM (-3)        /* device allocation failed                              */
+#define AGIS_E_TIMEOUT (-4)    /* a bounded device-side wait gave up                    */
+#define AGIS_E_NONFINITE (-5)  /* a non-finite value appeared in a reduction            */
+
+#define AGIS_N_CCD 62          /* astrometric-field CCDs (Sect. 3.4)                    */
+#define AGIS_N_ROW 7           /* across-scan CCD rows                                  */
+
+/* Instrument, ephemeris, epochs and knots (Sects. 3.2-3.4). */
+typedef struct agis_geometry {
+    double gamma_c;              /* conventional basic angle Gamma_c, Eq. srspropeta     */
+    double focal_length;         /* F (m), Eq. etazeta0                                  */
+    double p_ac;                 /* AC pixel size (m)                                    */
+    double mu_c;                 /* AC pixel coordinate of the CCD centre                */
+    double eta0[AGIS_N_CCD];     /* nominal AL observation line -Y_FPA/F per CCD (rad)   */
+    double x_fpa[AGIS_N_CCD];    /* X_FPA of the CCD centre (m)                          */
+    double x_centre[2];          /* X_FPA^centre[f]: index 0 for f = +1, 1 for f = -1    */
+    int32_t ccd_row[AGIS_N_CCD]; /* AC row of each CCD (0..6)                            */
+    double orb_L0;               /* ecliptic longitude of the observer at t = 0 (rad)   */
+    double obliquity;            /* ecliptic -> ICRS rotation angle (rad)                */
+    double au_light_s;           /* A_u / c (s)                                          */
+    double year_s;               /* length of the year for proper motions and the orbit  */
+    int64_t t_ep_ns;             /* reference epoch of the astrometric parameters        */
+    int64_t t_fr_ns;             /* frame rotator epoch (Eq. fr1)                        */
+    int64_t knot0_ns;            /* t_beg = tau_{M-1}: first regular knot (App. B.3)     */
+    int64_t knot_dt_ns;          /* uniform knot interval; 4-fold knots at both ends     */
+    int64_t cal_t0_ns;           /* start of the first calibration interval              */
+    int64_t cal_dt_ns;           /* length of the calibration intervals                  */
+    int32_t n_coef;              /* N: number of B-spline coefficients                   */
+    int32_t n_cal_days;          /* number of calibration intervals                      */
+} agis_geometry;
+
+/* Algorithm switches.  agis_default_config() fills the paper's values. */
+typedef struct agis_config {
+    int32_t robust;              /* 1: inner iteration with downweighting and excess noise (Sect. 5.1.2) */
+    int32_t n_rounds;            /* weight rounds of the inner iteration (4)             */
+    int32_t n_eps;               /* excess-noise steps per round (3)                     */
+    int32_t weight_fn;           /* 0: Eq. dw, 1: Huber Eq. dwH with c = 2               */
+    double lambda_att;           /* lambda of Eq. JfuncMod (1e-3)                        */
+    int32_t rhs_norm_term;       /* 1: lambda^2 dD D W also on the right-hand side       */
+    int32_t seg_len;             /* attitude segment length in knot intervals (Sect. 5.2.2) */
+    int32_t seg_overlap;         /* L (12): 2L overlapping knot intervals                */
+    int32_t frame_each_iter;     /* agis_iterate runs the frame rotator after each iteration */
+    int32_t block_mask;          /* bit 0: S, bit 1: A, bit 2: C (agis_iterate)          */
+    int32_t use_graph;           /* agis_iterate replays one captured CUDA graph per iteration */
+    double pivot_tol;            /* robust Cholesky: pivots <= pivot_tol * N_jj count as zero (1e-12) */
+    int32_t max_obs_per_source;  /* largest n_i accepted (bounds the S-pass scratch), 0: derived */
+    int32_t reserved[7];
+} agis_config;
+
+/* Observations in structure-of-arrays form, sorted by source index (ascending; any order
+ * within a source).  AL and AC components are separate observations (Sect. 3.6). */
+typedef struct agis_obs {
+    const int64_t* t_ns;         /* observation time                                     */
+    const int32_t* src;          /* source index 0..n_src-1                              */
+    const uint8_t* ccd;          /* AF CCD index 0..61                                   */
+    const uint8_t* fov;          /* 0: preceding field (f = +1), 1: following (f = -1)   */
+    const uint8_t* kind;         /* 0: AL (observed t), 1: AC (observed mu)              */
+    const float* sigma;          /* formal standard uncertainty (rad)                    */
+    const double* mu;            /* AC pixel coordinate (AC observations; AL ignored)    */
+} agis_obs;
+
+/* Statistics of one block call. */
+typedef struct agis_block_stats {
+    double chi2;                 /* sum_l W_l R_l^2 after the block                      */
+    double q_sum;                /* S: sum_i Q_i (Eq. Qi)                                */
+    int64_t nu_sum;              /* S: sum_i nu_i                                        */
+    int64_t n_out;               /* S: observations with w_l < 0.2                       */
+    int64_t rank_defect;         /* robust Cholesky rank-defect count (App. C)           */
+    double d_rms[5];             /* S: RMS of the 5 parameter updates                    */
+    double elapsed_ms;           /* device time of the block (CUDA events)               */
+} agis_block_stats;
+
+typedef struct agis_iter_stats {
+    agis_block_stats s, a, c;
+    double frame[6];             /* (eps, omega) applied by the frame rotator            */
+    double elapsed_ms;
+} agis_iter_stats;
+
+typedef struct agis_ctx agis_ctx;
+
+/* Fill cfg with the paper's defaults (4 rounds, 3 excess-noise steps, Eq. dw, lambda = 1e-3,
+ * L = 12, S[ACG] with the frame rotator each iteration). */
+void agis_default_config(agis_config* cfg);
+
+/* Create a context: validate and upload the observations (sorted by source), the starting
+ * values and the optional frame-rotator reference; build the time-ordered and
+ * calibration-ordered permutations.  Eq. synth, Sect. 3.6.
+ *   obs        n_obs observations (host or device pointers)
+ *   src0       n_src x 5 starting astrometric parameters
+ *   src_ref    n_src x 4 reference (alpha, delta, mu_a*, mu_d) at t_ep in the ICRS for the
+ *              frame rotator (subset S_PM of Sect. 6.1.4), or NULL (frame rotator disabled)
+ *   att0       n_coef x 4 starting spline coefficients
+ *   cal0       n_cal starting calibration offsets; n_cal = n_cal_days * 2 * (62 + 7):
+ *              AL offset of (interval d, field f, CCD n) at (d*2 + f)*62 + n,
+ *              AC offset of (d, f, row r) at n_cal_days*124 + (d*2 + f)*7 + r
+ *   stream     cudaStream_t to run on (NULL: the legacy default stream)
+ * Errors: AGIS_E_INVALID (unsorted sources, index out of range, non-finite input,
+ * n_coef < 4, inconsistent sizes), AGIS_E_OOM, AGIS_E_CUDA.  On error *out is NULL. */
+int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* obs, int64_t n_obs,
+              const double* src0, const double* src_ref, int32_t n_src, const double* att0, int32_t n_coef,
+              const double* cal0, int32_t n_cal, void* stream, agis_ctx** out);
+
+/* S block (Sect. 5.1): evaluate residuals and partials of every observation at the current
+ * (s, a, c) (Eqs. resAL, resAC, srsprop1diffsol, dfadq), solve the per-source 5x5 normal
+ * equations (Eq. normS) with the inner iteration, update s, and keep the residuals
+ * R_l = h_l - A_l d and weights W_l for the A and C blocks (Eq. precond2). */
+int agis_source_update(agis_ctx* ctx, agis_block_stats* out);
+
+/* A block (Sect. 5.2): banded attitude normals (Eq. normAmod) from the residuals and weights
+ * of the latest S block, segmented robust banded Cholesky (Sect. 5.2.2, App. C), update a.
+ * Error AGIS_E_INVALID if no S block ran since the context was created or restored. */
+int agis_attitude_update(agis_ctx* ctx, agis_block_stats* out);
+
+/* C block (Sect. 5.3): block-diagonal calibration normals (Eq. normC), robust solves and the
+ * constraint projection of Eq. calCon for Eqs. cc1 and cc3; update c.  Same call-order rule. */
+int agis_calibration_update(agis_ctx* ctx, agis_block_stats* out);
+
+/* Frame rotator (Sect. 6.1): least-squares (eps, omega) from Eq. cond-mu3 over all sources
+ * (or the n_subset listed in subset) with unit weights, then the rigorous transformation of
+ * the sources (Sect. 6.1.2) and a_n <- f(t_n)^-1 a_n (Eq. fr-q4).  eps_omega_out (6 doubles,
+ * host) receives the applied parameters.  AGIS_E_INVALID without a reference. */
+int agis_frame_rotate(agis_ctx* ctx, const int32_t* subset, int32_t n_subset, double eps_omega_out[6]);
+
+/* n_iter iterations of the S[ACG] simple iteration (Sects. 4.5-4.6) with the blocks of
+ * cfg->block_mask and, if cfg->frame_each_iter, the frame rotator.  per_iter (host, may be
+ * NULL) receives n_iter records; *n_done the number completed. */
+int agis_iterate(agis_ctx* ctx, int32_t n_iter, agis_iter_stats* per_iter, int32_t* n_done);
+
+/* Residuals R_l of all observations at the current (s, a, c) without updating anything
+ * (Eqs. resAL, resAC); out has n_obs doubles in the caller's observation order. */
+int agis_evaluate(agis_ctx* ctx, double* R_out);
+
+/* State export and checkpoint restore; buffers are caller-owned, sized as at agis_init. */
+int agis_get_sources(agis_ctx* ctx, double* src_out);           /* n_src x 5 */
+int agis_get_attitude(agis_ctx* ctx, double* att_out);          /* n_coef x 4 */
+int agis_get_calibration(agis_ctx* ctx, double* cal_out);       /* n_cal */
+int agis_set_sources(agis_ctx* ctx, const double* src);
+int agis_set_attitude(agis_ctx* ctx, const double* att);
+int agis_set_calibration(agis_ctx* ctx, const double* cal);
+/* Residuals and weights handed from the latest S block to A and C (caller order). */
+int agis_get_residuals(agis_ctx* ctx, double* R_out, double* W_out);
+/* Per-source results of the latest S block: eps_i^2, Q_i, nu_i, n_out_i, D_i (5 x n_src doubles,
+ * row-major by quantity) and the 5x5 inverse normal matrices (n_src x 25 doubles, or NULL). */
+int agis_get_source_stats(agis_ctx* ctx, double* stats_out, double* cov_out);
+
+/* Sizes of the context (n_obs, n_src, n_coef, n_cal). */
+int agis_get_sizes(const agis_ctx* ctx, int64_t* n_obs, int32_t* n_src, int32_t* n_coef, int32_t* n_cal);
+/* Device time in ms of the kernels of the latest call, per kernel class (S pass, A
+ * accumulation, A solve, C, frame): 5 doubles. */
+int agis_get_kernel_times(const agis_ctx* ctx, double* ms_out);
+
+void agis_destroy(agis_ctx* ctx);
+const char* agis_last_error(const agis_ctx* ctx);
+int agis_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGIS_H */

@@ -1,0 +1,832 @@
+// agis_api.cu -- the C ABI of include/agis.h: context, device memory, set-up of the
+// orderings (source, time / knot interval, calibration parameter) and the block calls.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "agis_internal.cuh"
+
+namespace agis {
+void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_ns, const uint32_t* meta,
+                          const float* sigma, const double* mu, const int64_t* src_off, const int32_t* src_order,
+                          int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out, ObsRec* rec,
+                          double* scratch, int cap, int* work_counter, int n_blocks, cudaStream_t stream);
+void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
+                     const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
+                     double* R, cudaStream_t stream);
+void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
+                      int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s);
+void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
+                      const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
+                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, cudaStream_t s);
+void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
+                double* dtil, int* rd, double* cal, cudaStream_t s);
+void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
+                  double* att, double* partial, int n_part, double tol, double* eo, cudaStream_t s);
+void launch_src_stats(int n_src, const double* chi2, const double* q, const int* nu, const int* nout, const int* rdf,
+                      const double* d, double* out, cudaStream_t s);
+void launch_int_sum(int n, const int* v, long long* out, cudaStream_t s);
+}  // namespace agis
+
+using namespace agis;
+
+// -----------------------------------------------------------------------------------------
+// set-up kernels
+// -----------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_validate_pack(int64_t n, const int64_t* __restrict__ t, const int32_t* __restrict__ src,
+                                const uint8_t* __restrict__ ccd, const uint8_t* __restrict__ fov,
+                                const uint8_t* __restrict__ kind, const float* __restrict__ sigma,
+                                const double* __restrict__ mu, int32_t n_src, int64_t cal_t0, int64_t cal_dt,
+                                int32_t n_days, const int32_t* __restrict__ ccd_row, uint32_t* __restrict__ meta,
+                                int* __restrict__ err) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = src[o];
+        const int c = ccd[o], f = fov[o], k = kind[o];
+        const float sg = sigma[o];
+        int bad = 0;
+        if (s < 0 || s >= n_src) bad |= 1;
+        if (o > 0 && src[o - 1] > s) bad |= 2;
+        if (c >= AGIS_N_CCD || f > 1 || k > 1) bad |= 4;
+        if (!(sg > 0.0f) || !isfinite(sg)) bad |= 8;
+        if (k == 1 && !isfinite(mu[o])) bad |= 16;
+        if (bad) atomicOr(err, bad);
+        const int64_t rel = t[o] - cal_t0;
+        int64_t day = rel < 0 ? 0 : rel / cal_dt;
+        if (day > n_days - 1) day = n_days - 1;
+        const int64_t kcal = k == 0 ? (day * 2 + f) * AGIS_N_CCD + c
+                                    : (int64_t)n_days * 124 + (day * 2 + f) * AGIS_N_ROW + ccd_row[c < AGIS_N_CCD ? c : 0];
+        meta[o] = (uint32_t)(c & 63) | ((uint32_t)f << 6) | ((uint32_t)k << 7) | ((uint32_t)kcal << 8);
+    }
+}
+
+__global__ void k_copy_mu(int64_t n, const uint8_t* __restrict__ kind, const double* __restrict__ mu_in,
+                          double* __restrict__ mu) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+        mu[o] = kind[o] ? mu_in[o] : 0.0;
+}
+
+__global__ void k_check_finite(int64_t n, const double* __restrict__ v, int* __restrict__ err, int code) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicOr(err, code);
+}
+
+// first index with key >= v in a sorted array (one thread per v)
+template <typename K>
+__global__ void k_lower_bound(const K* __restrict__ keys, int64_t n, int64_t n_out, int64_t* __restrict__ out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_out; v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)keys[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        out[v] = lo;
+    }
+}
+
+__global__ void k_interval_keys(DevGeo G, int64_t n, const int64_t* __restrict__ t, int32_t* __restrict__ key,
+                                uint32_t* __restrict__ val) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        key[o] = left_index(G, t[o]) - 3;
+        val[o] = (uint32_t)o;
+    }
+}
+
+__global__ void k_cal_keys(int64_t n, const uint32_t* __restrict__ meta, int32_t* __restrict__ key,
+                           uint32_t* __restrict__ val) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        key[o] = (int32_t)meta_cal(meta[o]);
+        val[o] = (uint32_t)o;
+    }
+}
+
+__global__ void k_src_counts(int32_t n_src, const int64_t* __restrict__ off, int32_t* __restrict__ negcount,
+                             int32_t* __restrict__ idx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        negcount[i] = -(int32_t)(off[i + 1] - off[i]);
+        idx[i] = i;
+    }
+}
+
+__global__ void k_rec_rw(int64_t n, const ObsRec* __restrict__ rec, double* __restrict__ R, double* __restrict__ W) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        if (R) R[o] = rec[o].R;
+        if (W) W[o] = rec[o].W;
+    }
+}
+
+__global__ void k_src_stats_out(int32_t n_src, const double* __restrict__ eps2, const double* __restrict__ q,
+                                const int* __restrict__ nu, const int* __restrict__ nout,
+                                const double* __restrict__ dsig, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        out[i] = eps2[i];
+        out[(size_t)n_src + i] = q[i];
+        out[2 * (size_t)n_src + i] = (double)nu[i];
+        out[3 * (size_t)n_src + i] = (double)nout[i];
+        out[4 * (size_t)n_src + i] = dsig[i];
+    }
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// -----------------------------------------------------------------------------------------
+// context
+// -----------------------------------------------------------------------------------------
+struct agis_ctx {
+    std::string err;
+    agis_geometry geo;
+    agis_config cfg;
+    DevGeo G;
+    Settings st;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_sm = 152;
+    int64_t n_obs = 0;
+    int32_t n_src = 0, n_coef = 0, n_cal = 0, n_days = 0;
+    std::vector<void*> allocs;
+    // observations (source order)
+    int64_t* t_ns = nullptr;
+    uint32_t* meta = nullptr;
+    float* sigma = nullptr;
+    double* mu = nullptr;
+    int32_t* obs_src = nullptr;
+    int64_t* src_off = nullptr;
+    int32_t* src_order = nullptr;
+    // state
+    double* src = nullptr;
+    double* ref = nullptr;
+    double* att = nullptr;
+    double* cal = nullptr;
+    // S block
+    ObsRec* rec = nullptr;
+    double* scratch = nullptr;
+    int cap = 0, n_sblocks = 0;
+    int* work = nullptr;
+    SrcOutPtrs so{};
+    double* sstats = nullptr;     // 10
+    // A block
+    uint32_t* perm_t = nullptr;
+    int64_t* ivl_off = nullptr;
+    int n_iv = 0;
+    double* blk = nullptr;
+    int n_seg = 0;
+    int64_t n_rows = 0;
+    int64_t* seg_row = nullptr;
+    int32_t *seg_l = nullptr, *seg_n = nullptr, *seg_u = nullptr;
+    double *bandc = nullptr, *rhs = nullptr, *urow = nullptr, *yv = nullptr, *xs = nullptr;
+    int* seg_rd = nullptr;
+    long long* isum = nullptr;    // [0] A rank defect, [1] C rank defect
+    // C block
+    uint32_t* perm_c = nullptr;
+    int64_t* cal_off = nullptr;
+    double* dtil = nullptr;
+    int* cal_rd = nullptr;
+    // frame rotator
+    double* fpart = nullptr;
+    int n_fpart = 0;
+    double* eo = nullptr;
+    int32_t* subset = nullptr;
+    int32_t subset_cap = 0;
+    double* evalR = nullptr;
+    double* tmpR = nullptr;
+    double* tmpW = nullptr;
+    // host read-back (pinned)
+    double* hstat = nullptr;      // 10 S + 6 frame
+    long long* hisum = nullptr;   // 2
+    bool have_s = false;
+    cudaEvent_t ev[12];
+    double ktimes[5] = {0, 0, 0, 0, 0};
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_frame = -1;
+    bool own_stream = false;
+    double* tmpS = nullptr;
+};
+
+namespace {
+
+int fail(agis_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(agis_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return AGIS_OK;
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? AGIS_E_OOM : AGIS_E_CUDA;
+}
+
+template <typename T>
+int dalloc(agis_ctx* c, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc");
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return AGIS_OK;
+}
+
+#define AGIS_TRY(x)                    \
+    do {                               \
+        int _r = (x);                  \
+        if (_r != AGIS_OK) return _r;  \
+    } while (0)
+#define AGIS_CU(c, x, what) AGIS_TRY(cuda_check((c), (x), (what)))
+
+// radix sort of (key, value) pairs, stable: the order within equal keys is the source order
+int sort_pairs(agis_ctx* c, int32_t* keys_in, int32_t* keys_out, uint32_t* vals_in, uint32_t* vals_out, int64_t n,
+               int end_bit) {
+    size_t tmp_bytes = 0;
+    AGIS_CU(c, cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, keys_out, vals_in, vals_out, n, 0, end_bit,
+                                               c->stream),
+            "cub sort (size)");
+    void* tmp = nullptr;
+    AGIS_CU(c, cudaMalloc(&tmp, tmp_bytes + 16), "cudaMalloc (sort)");
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, vals_out, n, 0,
+                                                    end_bit, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    AGIS_CU(c, e, "cub sort");
+    AGIS_CU(c, e2, "cub sort (sync)");
+    return AGIS_OK;
+}
+
+int bits_for(int64_t v) {
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) <= v) b++;
+    return b;
+}
+
+// overlapping attitude segments of Sect. 5.2.2 (same construction as the paper: cross-over
+// knots every seg_len intervals, 2L overlapping intervals, segment K updates a_n up to
+// n = x - floor(M/2))
+void build_segments(int n_coef, int seg_len, int L, std::vector<int32_t>& sl, std::vector<int32_t>& sn,
+                    std::vector<int32_t>& su, std::vector<int64_t>& srow) {
+    const int M = 4;
+    const int K = n_coef - M + 1;
+    const int S = seg_len;
+    const int nseg = std::max(1, (K + S - 1) / S);
+    srow.push_back(0);
+    for (int k = 0; k < nseg; k++) {
+        const int x0 = (M - 1) + k * S, x1 = (M - 1) + (k + 1) * S;
+        const int l_lo = std::max(M - 1, x0 - L);
+        const int l_hi = std::min(n_coef - 1, x1 + L - 1);
+        const int u_lo = k == 0 ? 0 : x0 - M / 2 + 1;
+        const int u_hi = k == nseg - 1 ? n_coef - 1 : x1 - M / 2;
+        sl.push_back(l_lo); sl.push_back(l_hi);
+        sn.push_back(l_lo - (M - 1)); sn.push_back(l_hi);
+        su.push_back(u_lo); su.push_back(u_hi);
+        srow.push_back(srow.back() + 4 * (int64_t)(l_hi - (l_lo - (M - 1)) + 1));
+    }
+}
+
+void record(agis_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
+double elapsed(agis_ctx* c, int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]);
+    return ms;
+}
+
+// --- the block sequences (enqueue only; no host synchronisation) ---------------------------
+void enqueue_s(agis_ctx* c) {
+    launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->src_off, c->src_order, c->n_src, c->att,
+                         c->cal, c->so, c->rec, c->scratch, c->cap, c->work, c->n_sblocks, c->stream);
+    launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
+                     c->stream);
+}
+void enqueue_a(agis_ctx* c) {
+    launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
+                     c->rec, c->att, c->blk, c->stream);
+    launch_att_solve(c->n_seg, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
+                     c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->stream);
+    launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
+}
+void enqueue_c(agis_ctx* c) {
+    launch_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->rec, c->st.pivot_tol, c->dtil,
+               c->cal_rd, c->cal, c->stream);
+    launch_int_sum(c->n_cal, c->cal_rd, c->isum + 1, c->stream);
+}
+void enqueue_frame(agis_ctx* c, const int32_t* subset, int n) {
+    launch_frame(c->G, n, subset, c->n_src, c->src, c->ref, c->att, c->fpart, c->n_fpart, c->st.pivot_tol, c->eo,
+                 c->stream);
+}
+
+void fill_s_stats(agis_ctx* c, const double* h, agis_block_stats* out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->chi2 = h[0];
+    out->q_sum = h[1];
+    out->nu_sum = (int64_t)llround(h[2]);
+    out->n_out = (int64_t)llround(h[3]);
+    out->rank_defect = (int64_t)llround(h[4]);
+    for (int k = 0; k < 5; k++) out->d_rms[k] = c->n_src > 0 ? std::sqrt(h[5 + k] / c->n_src) : 0.0;
+}
+
+}  // namespace
+
+// -----------------------------------------------------------------------------------------
+// ABI
+// -----------------------------------------------------------------------------------------
+extern "C" {
+
+int agis_abi_version(void) { return AGIS_ABI_VERSION; }
+
+void agis_default_config(agis_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->robust = 1;
+    cfg->n_rounds = 4;
+    cfg->n_eps = 3;
+    cfg->weight_fn = 0;
+    cfg->lambda_att = 1e-3;
+    cfg->rhs_norm_term = 0;
+    cfg->seg_len = 2880;
+    cfg->seg_overlap = 12;
+    cfg->frame_each_iter = 1;
+    cfg->block_mask = 7;
+    cfg->use_graph = 1;
+    cfg->pivot_tol = 1e-12;
+    cfg->max_obs_per_source = 0;
+}
+
+static thread_local std::string g_init_err = "no error";
+const char* agis_last_error(const agis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
+
+void agis_destroy(agis_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->hstat) cudaFreeHost(c->hstat);
+    if (c->hisum) cudaFreeHost(c->hisum);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    for (int i = 0; i < 12; i++)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    delete c;
+}
+
+int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* obs, int64_t n_obs, const double* src0,
+              const double* src_ref, int32_t n_src, const double* att0, int32_t n_coef, const double* cal0,
+              int32_t n_cal, void* stream, agis_ctx** out) {
+    if (!out) return AGIS_E_INVALID;
+    *out = nullptr;
+    agis_ctx* c = new agis_ctx();
+    for (int i = 0; i < 12; i++) c->ev[i] = nullptr;
+    auto bail = [&](int code) {
+        g_init_err = c->err;
+        agis_destroy(c);
+        return code;
+    };
+    if (!geo || !cfg || !obs || !src0 || !att0 || !cal0) return bail(fail(c, AGIS_E_INVALID, "null argument"));
+    if (n_obs < 0 || n_src < 0) return bail(fail(c, AGIS_E_INVALID, "negative size"));
+    if (n_obs >= ((int64_t)1 << 32)) return bail(fail(c, AGIS_E_INVALID, "more than 2^32-1 observations"));
+    if (n_coef < 4 || n_coef != geo->n_coef) return bail(fail(c, AGIS_E_INVALID, "n_coef < 4 or != geo->n_coef"));
+    if (geo->n_cal_days < 1 || n_cal != geo->n_cal_days * 2 * (AGIS_N_CCD + AGIS_N_ROW))
+        return bail(fail(c, AGIS_E_INVALID, "n_cal != n_cal_days * 138"));
+    if (geo->knot_dt_ns <= 0 || geo->cal_dt_ns <= 0 || !(geo->year_s > 0) || !(geo->focal_length > 0))
+        return bail(fail(c, AGIS_E_INVALID, "non-positive interval, year or focal length"));
+    if (n_obs > 0 && (!obs->t_ns || !obs->src || !obs->ccd || !obs->fov || !obs->kind || !obs->sigma || !obs->mu))
+        return bail(fail(c, AGIS_E_INVALID, "null observation array"));
+    if (cfg->seg_len < 1 || cfg->seg_overlap < 0 || cfg->n_rounds < 0 || cfg->n_eps < 0)
+        return bail(fail(c, AGIS_E_INVALID, "bad segmentation or iteration counts"));
+    for (int i = 0; i < AGIS_N_CCD; i++)
+        if (geo->ccd_row[i] < 0 || geo->ccd_row[i] >= AGIS_N_ROW) return bail(fail(c, AGIS_E_INVALID, "bad ccd_row"));
+    c->geo = *geo;
+    c->cfg = *cfg;
+    c->n_obs = n_obs;
+    c->n_src = n_src;
+    c->n_coef = n_coef;
+    c->n_cal = n_cal;
+    c->n_days = geo->n_cal_days;
+    c->stream = (cudaStream_t)stream;
+    if (!c->stream) {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(c, AGIS_E_CUDA, "cudaStreamCreate"));
+        c->own_stream = true;
+    }
+    if (cuda_check(c, cudaGetDevice(&c->device), "cudaGetDevice") != AGIS_OK) return bail(AGIS_E_CUDA);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    // device geometry
+    DevGeo& G = c->G;
+    std::memset(&G, 0, sizeof(G));
+    G.gamma_half = 0.5 * geo->gamma_c;
+    G.F = geo->focal_length;
+    G.p_ac = geo->p_ac;
+    G.mu_c = geo->mu_c;
+    for (int i = 0; i < AGIS_N_CCD; i++) {
+        G.eta0[i] = geo->eta0[i];
+        G.x_fpa[i] = geo->x_fpa[i];
+    }
+    G.x_centre[0] = geo->x_centre[0];
+    G.x_centre[1] = geo->x_centre[1];
+    G.orb_L0 = geo->orb_L0;
+    G.cos_obl = std::cos(geo->obliquity);
+    G.sin_obl = std::sin(geo->obliquity);
+    G.au_light_s = geo->au_light_s;
+    G.year_s = geo->year_s;
+    G.orb_rate = 2.0 * 3.141592653589793 / geo->year_s;
+    G.t_ep_ns = geo->t_ep_ns;
+    G.t_fr_ns = geo->t_fr_ns;
+    G.knot0_ns = geo->knot0_ns;
+    G.knot_dt_ns = geo->knot_dt_ns;
+    G.inv_knot_dt = 1.0 / (double)geo->knot_dt_ns;
+    G.n_coef = n_coef;
+    Settings& st = c->st;
+    st.robust = cfg->robust;
+    st.n_rounds = cfg->n_rounds;
+    st.n_eps = cfg->n_eps;
+    st.weight_fn = cfg->weight_fn;
+    st.lambda2 = cfg->lambda_att * cfg->lambda_att;
+    st.rhs_norm_term = cfg->rhs_norm_term;
+    st.pivot_tol = cfg->pivot_tol;
+    for (int i = 0; i < 12; i++) cudaEventCreate(&c->ev[i]);
+    if (cudaMallocHost(&c->hstat, 32 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->hisum, 4 * sizeof(long long)) != cudaSuccess)
+        return bail(fail(c, AGIS_E_OOM, "pinned host buffer"));
+    const int64_t n = n_obs;
+    // ---- observations
+    int* derr = nullptr;
+    int32_t* d_ccdrow = nullptr;
+    uint8_t *tmp8 = nullptr;
+    double* tmpmu = nullptr;
+    int rc = AGIS_OK;
+    if ((rc = dalloc(c, &c->t_ns, n)) || (rc = dalloc(c, &c->meta, n)) || (rc = dalloc(c, &c->sigma, n)) ||
+        (rc = dalloc(c, &c->mu, n)) || (rc = dalloc(c, &c->obs_src, n)) || (rc = dalloc(c, &derr, 1)) ||
+        (rc = dalloc(c, &d_ccdrow, AGIS_N_CCD)) || (rc = dalloc(c, &tmp8, 3 * (size_t)n + 16)) ||
+        (rc = dalloc(c, &tmpmu, n)))
+        return bail(rc);
+    cudaStream_t s = c->stream;
+#define CP(dst, srcp, bytes)                                                                          \
+    if (cuda_check(c, cudaMemcpyAsync((dst), (srcp), (bytes), cudaMemcpyDefault, s), "copy inputs")) \
+        return bail(AGIS_E_CUDA);
+    if (n > 0) {
+        CP(c->t_ns, obs->t_ns, n * sizeof(int64_t));
+        CP(c->obs_src, obs->src, n * sizeof(int32_t));
+        CP(tmp8, obs->ccd, n);
+        CP(tmp8 + n, obs->fov, n);
+        CP(tmp8 + 2 * n, obs->kind, n);
+        CP(c->sigma, obs->sigma, n * sizeof(float));
+        CP(tmpmu, obs->mu, n * sizeof(double));
+    }
+    CP(d_ccdrow, geo->ccd_row, AGIS_N_CCD * sizeof(int32_t));
+    cudaMemsetAsync(derr, 0, sizeof(int), s);
+    if (n > 0) {
+        k_validate_pack<<<grid_for(n, 256), 256, 0, s>>>(n, c->t_ns, c->obs_src, tmp8, tmp8 + n, tmp8 + 2 * n,
+                                                         c->sigma, tmpmu, n_src, geo->cal_t0_ns, geo->cal_dt_ns,
+                                                         geo->n_cal_days, d_ccdrow, c->meta, derr);
+        k_copy_mu<<<grid_for(n, 256), 256, 0, s>>>(n, tmp8 + 2 * n, tmpmu, c->mu);
+    }
+    // ---- state
+    if ((rc = dalloc(c, &c->src, 5 * (size_t)n_src)) || (rc = dalloc(c, &c->att, 4 * (size_t)n_coef)) ||
+        (rc = dalloc(c, &c->cal, n_cal)))
+        return bail(rc);
+    CP(c->src, src0, 5 * (size_t)n_src * sizeof(double));
+    CP(c->att, att0, 4 * (size_t)n_coef * sizeof(double));
+    CP(c->cal, cal0, (size_t)n_cal * sizeof(double));
+    if (src_ref) {
+        if ((rc = dalloc(c, &c->ref, 4 * (size_t)n_src))) return bail(rc);
+        CP(c->ref, src_ref, 4 * (size_t)n_src * sizeof(double));
+    }
+    k_check_finite<<<grid_for(5 * (int64_t)n_src, 256), 256, 0, s>>>(5 * (int64_t)n_src, c->src, derr, 32);
+    k_check_finite<<<grid_for(4 * (int64_t)n_coef, 256), 256, 0, s>>>(4 * (int64_t)n_coef, c->att, derr, 32);
+    k_check_finite<<<grid_for(n_cal, 256), 256, 0, s>>>(n_cal, c->cal, derr, 32);
+    int herr = 0;
+    if (cuda_check(c, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s), "validate") ||
+        cuda_check(c, cudaStreamSynchronize(s), "validate (sync)"))
+        return bail(AGIS_E_CUDA);
+    if (herr) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "invalid input (flags 0x%x: 1 source index out of range, 2 not sorted by source, "
+                      "4 ccd/fov/kind out of range, 8 sigma not positive, 16 mu not finite, 32 non-finite state)",
+                      herr);
+        return bail(fail(c, AGIS_E_INVALID, buf));
+    }
+    // ---- source offsets, largest-first order, scratch capacity
+    if ((rc = dalloc(c, &c->src_off, (size_t)n_src + 1)) || (rc = dalloc(c, &c->src_order, n_src))) return bail(rc);
+    k_lower_bound<int32_t><<<grid_for(n_src + 1, 256), 256, 0, s>>>(c->obs_src, n, (int64_t)n_src + 1, c->src_off);
+    std::vector<int64_t> hoff((size_t)n_src + 1);
+    if (cuda_check(c, cudaMemcpyAsync(hoff.data(), c->src_off, hoff.size() * 8, cudaMemcpyDeviceToHost, s), "offsets") ||
+        cuda_check(c, cudaStreamSynchronize(s), "offsets (sync)"))
+        return bail(AGIS_E_CUDA);
+    int64_t maxn = 0;
+    for (int32_t i = 0; i < n_src; i++) maxn = std::max(maxn, hoff[i + 1] - hoff[i]);
+    if (cfg->max_obs_per_source > 0) {
+        if (maxn > cfg->max_obs_per_source)
+            return bail(fail(c, AGIS_E_INVALID, "a source has more observations than max_obs_per_source"));
+        maxn = cfg->max_obs_per_source;
+    }
+    c->cap = (int)std::max<int64_t>(maxn, 32);
+    {
+        int32_t *k_in = nullptr, *k_out = nullptr, *i_in = nullptr;
+        if ((rc = dalloc(c, &k_in, n_src)) || (rc = dalloc(c, &k_out, n_src)) || (rc = dalloc(c, &i_in, n_src)))
+            return bail(rc);
+        k_src_counts<<<grid_for(n_src, 256), 256, 0, s>>>(n_src, c->src_off, k_in, i_in);
+        if (n_src > 0 && (rc = sort_pairs(c, k_in, k_out, (uint32_t*)i_in, (uint32_t*)c->src_order, n_src, 32)))
+            return bail(rc);
+    }
+    c->n_sblocks = c->n_sm * 4;
+    {
+        size_t want = (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr * sizeof(double);
+        const size_t limit = (size_t)8 << 30;
+        while (want > limit && c->n_sblocks > c->n_sm) {
+            c->n_sblocks /= 2;
+            want = (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr * sizeof(double);
+        }
+    }
+    if ((rc = dalloc(c, &c->rec, n)) ||
+        (rc = dalloc(c, &c->scratch, (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr)) ||
+        (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
+        (rc = dalloc(c, &c->so.eps2, n_src)) || (rc = dalloc(c, &c->so.q, n_src)) ||
+        (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||
+        (rc = dalloc(c, &c->so.cov, 25 * (size_t)n_src)) || (rc = dalloc(c, &c->so.nu, n_src)) ||
+        (rc = dalloc(c, &c->so.nout, n_src)) || (rc = dalloc(c, &c->so.rankdef, n_src)) ||
+        (rc = dalloc(c, &c->sstats, 16)))
+        return bail(rc);
+    c->so.src = c->src;
+    // ---- time order by knot interval
+    c->n_iv = n_coef - 3;
+    {
+        int32_t *k_in = nullptr, *k_out = nullptr;
+        uint32_t* v_in = nullptr;
+        if ((rc = dalloc(c, &k_in, n)) || (rc = dalloc(c, &k_out, n)) || (rc = dalloc(c, &v_in, n)) ||
+            (rc = dalloc(c, &c->perm_t, n)) || (rc = dalloc(c, &c->ivl_off, (size_t)c->n_iv + 1)))
+            return bail(rc);
+        if (n > 0) {
+            k_interval_keys<<<grid_for(n, 256), 256, 0, s>>>(G, n, c->t_ns, k_in, v_in);
+            if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_t, n, bits_for(c->n_iv)))) return bail(rc);
+        }
+        k_lower_bound<int32_t><<<grid_for(c->n_iv + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)c->n_iv + 1, c->ivl_off);
+        // calibration order
+        if ((rc = dalloc(c, &c->perm_c, n)) || (rc = dalloc(c, &c->cal_off, (size_t)n_cal + 1))) return bail(rc);
+        if (n > 0) {
+            k_cal_keys<<<grid_for(n, 256), 256, 0, s>>>(n, c->meta, k_in, v_in);
+            if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_c, n, bits_for(n_cal)))) return bail(rc);
+        }
+        k_lower_bound<int32_t><<<grid_for(n_cal + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)n_cal + 1, c->cal_off);
+    }
+    // ---- segments and band storage
+    {
+        std::vector<int32_t> sl, sn, su;
+        std::vector<int64_t> srow;
+        build_segments(n_coef, cfg->seg_len, cfg->seg_overlap, sl, sn, su, srow);
+        c->n_seg = (int)(srow.size() - 1);
+        c->n_rows = srow.back();
+        if ((rc = dalloc(c, &c->seg_row, srow.size())) || (rc = dalloc(c, &c->seg_l, sl.size())) ||
+            (rc = dalloc(c, &c->seg_n, sn.size())) || (rc = dalloc(c, &c->seg_u, su.size())) ||
+            (rc = dalloc(c, &c->blk, (size_t)c->n_iv * kBlkVals)) || (rc = dalloc(c, &c->bandc, 16 * (size_t)c->n_rows)) ||
+            (rc = dalloc(c, &c->rhs, c->n_rows)) || (rc = dalloc(c, &c->urow, 16 * (size_t)c->n_rows)) ||
+            (rc = dalloc(c, &c->yv, c->n_rows)) || (rc = dalloc(c, &c->xs, c->n_rows)) ||
+            (rc = dalloc(c, &c->seg_rd, c->n_seg)) || (rc = dalloc(c, &c->isum, 4)))
+            return bail(rc);
+        CP(c->seg_row, srow.data(), srow.size() * sizeof(int64_t));
+        CP(c->seg_l, sl.data(), sl.size() * sizeof(int32_t));
+        CP(c->seg_n, sn.data(), sn.size() * sizeof(int32_t));
+        CP(c->seg_u, su.data(), su.size() * sizeof(int32_t));
+    }
+    if ((rc = dalloc(c, &c->dtil, n_cal)) || (rc = dalloc(c, &c->cal_rd, n_cal))) return bail(rc);
+    c->n_fpart = std::min(1024, std::max(1, (n_src + 255) / 256));
+    if ((rc = dalloc(c, &c->fpart, (size_t)c->n_fpart * 27)) || (rc = dalloc(c, &c->eo, 8))) return bail(rc);
+    if (cuda_check(c, cudaStreamSynchronize(s), "init") || cuda_check(c, cudaGetLastError(), "init kernels"))
+        return bail(AGIS_E_CUDA);
+#undef CP
+    *out = c;
+    return AGIS_OK;
+}
+
+int agis_source_update(agis_ctx* c, agis_block_stats* out) {
+    if (!c) return AGIS_E_INVALID;
+    record(c, 0);
+    enqueue_s(c);
+    record(c, 1);
+    AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "stats");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "source update");
+    AGIS_CU(c, cudaGetLastError(), "source update kernels");
+    c->have_s = true;
+    fill_s_stats(c, c->hstat, out);
+    c->ktimes[0] = elapsed(c, 0, 1);
+    if (out) out->elapsed_ms = c->ktimes[0];
+    if (!std::isfinite(c->hstat[0])) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2 after the source update");
+    return AGIS_OK;
+}
+
+int agis_attitude_update(agis_ctx* c, agis_block_stats* out) {
+    if (!c) return AGIS_E_INVALID;
+    if (!c->have_s) return fail(c, AGIS_E_INVALID, "attitude update needs a source update first");
+    record(c, 2);
+    enqueue_a(c);
+    record(c, 3);
+    AGIS_CU(c, cudaMemcpyAsync(c->hisum, c->isum, sizeof(long long), cudaMemcpyDeviceToHost, c->stream), "stats");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "attitude update");
+    AGIS_CU(c, cudaGetLastError(), "attitude update kernels");
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->rank_defect = c->hisum[0];
+        out->elapsed_ms = elapsed(c, 2, 3);
+    }
+    c->ktimes[2] = elapsed(c, 2, 3);
+    return AGIS_OK;
+}
+
+int agis_calibration_update(agis_ctx* c, agis_block_stats* out) {
+    if (!c) return AGIS_E_INVALID;
+    if (!c->have_s) return fail(c, AGIS_E_INVALID, "calibration update needs a source update first");
+    record(c, 4);
+    enqueue_c(c);
+    record(c, 5);
+    AGIS_CU(c, cudaMemcpyAsync(c->hisum + 1, c->isum + 1, sizeof(long long), cudaMemcpyDeviceToHost, c->stream),
+            "stats");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "calibration update");
+    AGIS_CU(c, cudaGetLastError(), "calibration update kernels");
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->rank_defect = c->hisum[1];
+        out->elapsed_ms = elapsed(c, 4, 5);
+    }
+    c->ktimes[3] = elapsed(c, 4, 5);
+    return AGIS_OK;
+}
+
+int agis_frame_rotate(agis_ctx* c, const int32_t* subset, int32_t n_subset, double eps_omega_out[6]) {
+    if (!c) return AGIS_E_INVALID;
+    if (!c->ref) return fail(c, AGIS_E_INVALID, "no frame-rotator reference given at agis_init");
+    const int32_t* dsub = nullptr;
+    int nn = c->n_src;
+    if (subset) {
+        if (n_subset < 0) return fail(c, AGIS_E_INVALID, "negative subset size");
+        if (n_subset > c->subset_cap) {
+            int rc = dalloc(c, &c->subset, (size_t)n_subset);
+            if (rc) return rc;
+            c->subset_cap = n_subset;
+        }
+        std::vector<int32_t> h(subset, subset + n_subset);
+        for (int32_t v : h)
+            if (v < 0 || v >= c->n_src) return fail(c, AGIS_E_INVALID, "subset index out of range");
+        AGIS_CU(c, cudaMemcpyAsync(c->subset, h.data(), n_subset * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+                "subset");
+        dsub = c->subset;
+        nn = n_subset;
+    }
+    record(c, 6);
+    enqueue_frame(c, dsub, nn);
+    record(c, 7);
+    AGIS_CU(c, cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "frame");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "frame rotator");
+    AGIS_CU(c, cudaGetLastError(), "frame rotator kernels");
+    if (eps_omega_out)
+        for (int i = 0; i < 6; i++) eps_omega_out[i] = c->hstat[16 + i];
+    c->ktimes[4] = elapsed(c, 6, 7);
+    c->have_s = false;  // the residuals of the last S block refer to the unrotated frame
+    return AGIS_OK;
+}
+
+int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t* n_done) {
+    if (!c) return AGIS_E_INVALID;
+    if (n_done) *n_done = 0;
+    const bool do_frame = c->cfg.frame_each_iter && c->ref;
+    const int mask = c->cfg.block_mask;
+    auto enqueue_iter = [&]() {
+        record(c, 8);
+        if (mask & 1) enqueue_s(c);
+        record(c, 9);
+        if (mask & 2) enqueue_a(c);
+        record(c, 10);
+        if (mask & 4) enqueue_c(c);
+        if (do_frame) enqueue_frame(c, nullptr, c->n_src);
+        record(c, 11);
+        cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(c->hisum, c->isum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+        if (do_frame) cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    };
+    if (!(mask & 1) && (mask & 6) && !c->have_s)
+        return fail(c, AGIS_E_INVALID, "A/C blocks without an S block need a prior source update");
+    cudaMemsetAsync(c->isum, 0, 2 * sizeof(long long), c->stream);
+    const bool graph = c->cfg.use_graph != 0;
+    if (graph && c->graph_exec && c->graph_frame != (int)do_frame) {
+        cudaGraphExecDestroy(c->graph_exec);
+        cudaGraphDestroy(c->graph);
+        c->graph_exec = nullptr;
+        c->graph = nullptr;
+    }
+    if (graph && !c->graph_exec) {
+        AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        enqueue_iter();
+        AGIS_CU(c, cudaStreamEndCapture(c->stream, &c->graph), "end capture");
+        AGIS_CU(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0), "instantiate graph");
+        c->graph_frame = (int)do_frame;
+    }
+    for (int32_t k = 0; k < n_iter; k++) {
+        if (graph) {
+            AGIS_CU(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+        } else {
+            enqueue_iter();
+        }
+        AGIS_CU(c, cudaStreamSynchronize(c->stream), "iteration");
+        AGIS_CU(c, cudaGetLastError(), "iteration kernels");
+        if (mask & 1) c->have_s = !do_frame;
+        if (per_iter) {
+            agis_iter_stats& it = per_iter[k];
+            std::memset(&it, 0, sizeof(it));
+            if (mask & 1) fill_s_stats(c, c->hstat, &it.s);
+            it.a.rank_defect = c->hisum[0];
+            it.c.rank_defect = c->hisum[1];
+            if (do_frame)
+                for (int i = 0; i < 6; i++) it.frame[i] = c->hstat[16 + i];
+            it.s.elapsed_ms = elapsed(c, 8, 9);
+            it.a.elapsed_ms = elapsed(c, 9, 10);
+            it.elapsed_ms = elapsed(c, 8, 11);
+        }
+        if ((mask & 1) && !std::isfinite(c->hstat[0])) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2");
+        if (n_done) *n_done = k + 1;
+    }
+    return AGIS_OK;
+}
+
+int agis_evaluate(agis_ctx* c, double* R_out) {
+    if (!c || !R_out) return AGIS_E_INVALID;
+    if (!c->evalR) AGIS_TRY(dalloc(c, &c->evalR, (size_t)c->n_obs));
+    launch_evaluate(c->G, c->t_ns, c->meta, c->mu, c->obs_src, c->n_obs, c->src, c->att, c->cal, c->evalR, c->stream);
+    AGIS_CU(c, cudaMemcpyAsync(R_out, c->evalR, c->n_obs * sizeof(double), cudaMemcpyDefault, c->stream), "copy R");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "evaluate");
+    return cuda_check(c, cudaGetLastError(), "evaluate kernels");
+}
+
+static int get_copy(agis_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (!c || !dst) return AGIS_E_INVALID;
+    AGIS_CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
+    return AGIS_OK;
+}
+
+int agis_get_sources(agis_ctx* c, double* o) { return c ? get_copy(c, o, c->src, 5 * (size_t)c->n_src * 8) : AGIS_E_INVALID; }
+int agis_get_attitude(agis_ctx* c, double* o) { return c ? get_copy(c, o, c->att, 4 * (size_t)c->n_coef * 8) : AGIS_E_INVALID; }
+int agis_get_calibration(agis_ctx* c, double* o) { return c ? get_copy(c, o, c->cal, (size_t)c->n_cal * 8) : AGIS_E_INVALID; }
+
+static int set_copy(agis_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (!c || !src) return AGIS_E_INVALID;
+    AGIS_CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
+    c->have_s = false;
+    return AGIS_OK;
+}
+int agis_set_sources(agis_ctx* c, const double* v) { return c ? set_copy(c, c->src, v, 5 * (size_t)c->n_src * 8) : AGIS_E_INVALID; }
+int agis_set_attitude(agis_ctx* c, const double* v) { return c ? set_copy(c, c->att, v, 4 * (size_t)c->n_coef * 8) : AGIS_E_INVALID; }
+int agis_set_calibration(agis_ctx* c, const double* v) { return c ? set_copy(c, c->cal, v, (size_t)c->n_cal * 8) : AGIS_E_INVALID; }
+
+int agis_get_residuals(agis_ctx* c, double* R_out, double* W_out) {
+    if (!c) return AGIS_E_INVALID;
+    if (!c->have_s) return fail(c, AGIS_E_INVALID, "no source update since the last state change");
+    if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
+    if (!c->tmpW) AGIS_TRY(dalloc(c, &c->tmpW, (size_t)c->n_obs));
+    k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->rec, c->tmpR, c->tmpW);
+    if (R_out) AGIS_CU(c, cudaMemcpyAsync(R_out, c->tmpR, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy R");
+    if (W_out) AGIS_CU(c, cudaMemcpyAsync(W_out, c->tmpW, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy W");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "residuals");
+    return AGIS_OK;
+}
+
+int agis_get_source_stats(agis_ctx* c, double* stats_out, double* cov_out) {
+    if (!c) return AGIS_E_INVALID;
+    if (stats_out) {
+        if (!c->tmpS) AGIS_TRY(dalloc(c, &c->tmpS, 5 * (size_t)c->n_src));
+        double* buf = c->tmpS;
+        k_src_stats_out<<<grid_for(c->n_src, 256), 256, 0, c->stream>>>(c->n_src, c->so.eps2, c->so.q, c->so.nu,
+                                                                       c->so.nout, c->so.dsig, buf);
+        AGIS_TRY(get_copy(c, stats_out, buf, 5 * (size_t)c->n_src * 8));
+    }
+    if (cov_out) AGIS_TRY(get_copy(c, cov_out, c->so.cov, 25 * (size_t)c->n_src * 8));
+    return AGIS_OK;
+}
+
+int agis_get_sizes(const agis_ctx* c, int64_t* n_obs, int32_t* n_src, int32_t* n_coef, int32_t* n_cal) {
+    if (!c) return AGIS_E_INVALID;
+    if (n_obs) *n_obs = c->n_obs;
+    if (n_src) *n_src = c->n_src;
+    if (n_coef) *n_coef = c->n_coef;
+    if (n_cal) *n_cal = c->n_cal;
+    return AGIS_OK;
+}
+
+int agis_get_kernel_times(const agis_ctx* c, double* ms) {
+    if (!c || !ms) return AGIS_E_INVALID;
+    for (int i = 0; i < 5; i++) ms[i] = c->ktimes[i];
+    return AGIS_OK;
+}
+
+}  // extern "C"

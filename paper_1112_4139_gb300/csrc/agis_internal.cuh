@@ -1,0 +1,336 @@
+// agis_internal.cuh -- device-side data layout and the per-observation model of the AGIS
+// hot path (Lindegren et al. 2012).  Shared by the kernels of this library only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "agis.h"
+
+namespace agis {
+
+constexpr int kWarp = 32;
+constexpr int kNccd = AGIS_N_CCD;
+constexpr int kRecDoubles = 8;   // A/C hand-over record: 64 bytes per observation
+constexpr int kBlkVals = 152;    // per knot interval: 136 upper entries of the 16x16 + 16 rhs
+constexpr int kScr = 8;          // S-pass scratch per observation: h, A[5], w, sigma^2
+
+// Packed per-observation descriptor: bits 0-5 CCD, 6 field (0: f=+1), 7 kind (0: AL),
+// 8-31 calibration parameter index.
+__host__ __device__ inline uint32_t meta_ccd(uint32_t m) { return m & 63u; }
+__host__ __device__ inline uint32_t meta_fov(uint32_t m) { return (m >> 6) & 1u; }
+__host__ __device__ inline uint32_t meta_kind(uint32_t m) { return (m >> 7) & 1u; }
+__host__ __device__ inline uint32_t meta_cal(uint32_t m) { return m >> 8; }
+
+// Geometry passed by value to the kernels.
+struct DevGeo {
+    double gamma_half;
+    double F, p_ac, mu_c;
+    double eta0[kNccd];
+    double x_fpa[kNccd];
+    double x_centre[2];
+    double orb_L0, cos_obl, sin_obl, au_light_s, year_s, orb_rate;
+    int64_t t_ep_ns, t_fr_ns, knot0_ns, knot_dt_ns;
+    double inv_knot_dt;
+    int32_t n_coef;
+};
+
+// Hand-over record written by the S pass and read (gathered) by the A and C passes.
+struct __align__(16) ObsRec {
+    int64_t t_ns;
+    double R;       // residual after the source update, h - A d
+    double W;       // statistical weight w / (sigma^2 + eps^2)
+    uint32_t meta;
+    int32_t pad;
+    double g[4];    // dR/dq / ||s||  (so that dR/da_n = g B_n)
+};
+static_assert(sizeof(ObsRec) == 64, "record must be 64 bytes");
+
+// Per-source outputs of the S block (device arrays).
+struct SrcOutPtrs {
+    double* src;      // n_src x 5, updated in place
+    double* d;        // n_src x 5 updates
+    double* eps2;     // excess source variance
+    double* q;        // Q_i
+    double* dsig;     // significance D
+    double* chi2;     // sum over the source of W R^2
+    double* cov;      // n_src x 25 inverse normal matrix
+    int* nu;
+    int* nout;
+    int* rankdef;
+};
+
+struct Settings {
+    int robust, n_rounds, n_eps, weight_fn;
+    double lambda2;
+    int rhs_norm_term;
+    double pivot_tol;
+};
+
+// ---------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Downweighting factor, Eq. dw (weight_fn 0) or Huber Eq. dwH with c = 2 (weight_fn 1).
+__device__ __forceinline__ double wfun(double z, int fn) {
+    double a = fabs(z);
+    if (fn == 0) {
+        if (a <= 2.0) return 1.0;
+        if (a < 3.0) {
+            double t = a - 2.0;
+            return 1.0 - 1.773735 * t * t + 1.141615 * t * t * t;
+        }
+        return exp(-a / 3.0);
+    }
+    if (a <= 2.0) return 1.0;
+    return 2.0 * (2.0 * a - 2.0) / (a * a);
+}
+
+// knot tau_k (ns) of the uniform sequence with 4-fold end knots
+__device__ __forceinline__ int64_t knot_at(const DevGeo& G, int64_t k) {
+    int64_t K = (int64_t)G.n_coef - 3;
+    int64_t j = k - 3;
+    j = j < 0 ? 0 : (j > K ? K : j);
+    return G.knot0_ns + j * G.knot_dt_ns;
+}
+
+__device__ __forceinline__ int left_index(const DevGeo& G, int64_t t) {
+    int64_t rel = t - G.knot0_ns;
+    if (rel < 0) return 3;
+    int64_t l = 3 + rel / G.knot_dt_ns;
+    if (l > G.n_coef - 1) l = G.n_coef - 1;
+    return (int)l;
+}
+
+// The four non-zero cubic B-splines B_{l-3..l}(t) (App. B): closed form where the six
+// knots around the interval are regular, Algorithm B.1 near the multiple end knots.
+__device__ __forceinline__ void bspline4(const DevGeo& G, int64_t t, int l, double b[4]) {
+    if (l >= 5 && l <= G.n_coef - 3) {
+        double u = (double)(t - knot_at(G, l)) * G.inv_knot_dt;
+        double v = 1.0 - u;
+        double u2 = u * u, u3 = u2 * u;
+        b[0] = v * v * v * (1.0 / 6.0);
+        b[1] = (3.0 * u3 - 6.0 * u2 + 4.0) * (1.0 / 6.0);
+        b[2] = (-3.0 * u3 + 3.0 * u2 + 3.0 * u + 1.0) * (1.0 / 6.0);
+        b[3] = u3 * (1.0 / 6.0);
+        return;
+    }
+    double R[3], L[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        R[i] = (double)(knot_at(G, l + i + 1) - t);
+        L[i] = (double)(t - knot_at(G, l - i));
+    }
+    b[0] = 1.0; b[1] = b[2] = b[3] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            double u = b[j] / (R[j] + L[i - j]);
+            b[j] = s + R[j] * u;
+            s = L[i - j] * u;
+        }
+        b[i + 1] = s;
+    }
+}
+
+// quaternion product ab, Eq. quatmult
+__device__ __forceinline__ void qmul(const double* a, const double* b, double* c) {
+    c[0] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    c[1] = -a[0] * b[2] + a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    c[2] = a[0] * b[1] - a[1] * b[0] + a[2] * b[3] + a[3] * b[2];
+    c[3] = -a[0] * b[0] - a[1] * b[1] - a[2] * b[2] + a[3] * b[3];
+}
+
+// attitude matrix of a unit quaternion, Eq. quat2mat (rows: SRS axes in the ICRS)
+__device__ __forceinline__ void quat2mat(const double* q, double m[9]) {
+    double x = q[0], y = q[1], z = q[2], w = q[3];
+    m[0] = 1.0 - 2.0 * (y * y + z * z); m[1] = 2.0 * (x * y + z * w); m[2] = 2.0 * (x * z - y * w);
+    m[3] = 2.0 * (x * y - z * w); m[4] = 1.0 - 2.0 * (x * x + z * z); m[5] = 2.0 * (y * z + x * w);
+    m[6] = 2.0 * (x * z + y * w); m[7] = 2.0 * (y * z - x * w); m[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// Per-source geometry: normal triad (Eq. normal-triad) and the parameters.
+struct SrcGeo {
+    double p[3], q[3], r[3];
+    double par, pma, pmd, cosd;
+};
+
+__device__ __forceinline__ void source_geo(const double* s5, SrcGeo& S) {
+    double sa, ca, sd, cd;
+    sincos(s5[0], &sa, &ca);
+    sincos(s5[1], &sd, &cd);
+    S.p[0] = -sa; S.p[1] = ca; S.p[2] = 0.0;
+    S.q[0] = -sd * ca; S.q[1] = -sd * sa; S.q[2] = cd;
+    S.r[0] = cd * ca; S.r[1] = cd * sa; S.r[2] = sd;
+    S.par = s5[2]; S.pma = s5[3]; S.pmd = s5[4];
+    S.cosd = cd;
+}
+
+struct ObsOut {
+    double R;       // residual
+    double A[5];    // -dR/ds'
+    double g[4];    // dR/dq / ||s||
+};
+
+// Residual and partial derivatives of one observation (FP64).
+//   proper direction: Eqs. astro-standard, roemer, classAberr
+//   field angles: Eqs. srsprop, srsprop1, srspropeta; lines: Eqs. etazeta0, etazeta (r = 0)
+//   source partials: Eqs. srspqr, srsprop1diffsol, ubardiff, duds (evaluated in the ICRS by
+//   turning m and n back with the attitude matrix)
+//   attitude partials: Eq. dfadq divided by ||s|| (normalisation of Eq. qspline)
+template <bool kPartials>
+__device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_t t, uint32_t meta, double mu,
+                                        const double* __restrict__ att, const double* __restrict__ cal,
+                                        ObsOut& o) {
+    // ephemeris: circular orbit, ICRS components (AU, AU/s)
+    double ts = (double)t * 1e-9;
+    double Lang = G.orb_L0 + 2.0 * 3.141592653589793 * (ts / G.year_s);
+    double sL, cL;
+    sincos(Lang, &sL, &cL);
+    double b[3] = {cL, G.cos_obl * sL, G.sin_obl * sL};
+    double vc[3] = {-G.orb_rate * sL * G.au_light_s, G.cos_obl * G.orb_rate * cL * G.au_light_s,
+                    G.sin_obl * G.orb_rate * cL * G.au_light_s};
+    // Roemer delay and proper-motion time
+    double rb = dot3(S.r, b);
+    double tau = ((double)(t - G.t_ep_ns) * 1e-9 + rb * G.au_light_s) / G.year_s;
+    double ub[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) ub[i] = S.r[i] + tau * (S.p[i] * S.pma + S.q[i] * S.pmd) - S.par * b[i];
+    double nb = sqrt(dot3(ub, ub));
+    ub[0] /= nb; ub[1] /= nb; ub[2] /= nb;
+    double u[3] = {ub[0] + vc[0], ub[1] + vc[1], ub[2] + vc[2]};
+    double nu = sqrt(dot3(u, u));
+    u[0] /= nu; u[1] /= nu; u[2] /= nu;
+    // attitude
+    int l = left_index(G, t);
+    double B[4];
+    bspline4(G, t, l, B);
+    const double* a = att + 4 * (int64_t)(l - 3);
+    double s[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
+    double ns = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+    double q[4] = {s[0] / ns, s[1] / ns, s[2] / ns, s[3] / ns};
+    double Am[9];
+    quat2mat(q, Am);
+    double us[3] = {dot3(Am, u), dot3(Am + 3, u), dot3(Am + 6, u)};
+    double phi = atan2(us[1], us[0]);
+    double rho = sqrt(us[0] * us[0] + us[1] * us[1]);
+    double zeta = atan2(us[2], rho);
+    uint32_t fov = meta_fov(meta), kind = meta_kind(meta), ccd = meta_ccd(meta);
+    double f = fov == 0 ? 1.0 : -1.0;
+    double c_k = cal[meta_cal(meta)];
+    if (kind == 0) {
+        double eta = phi - f * G.gamma_half;
+        o.R = (G.eta0[ccd] + c_k) - eta;
+    } else {
+        double zeta0 = -(G.x_fpa[ccd] - (mu - G.mu_c) * G.p_ac - G.x_centre[fov]) / G.F;
+        o.R = (zeta0 + c_k) - zeta;
+    }
+    if (!kPartials) return;
+    // m, n in the SRS (Eq. srspqr) from the components of S'u
+    double cphi = us[0] / rho, sphi = us[1] / rho;
+    double czeta = rho, szeta = us[2];
+    double ms[3] = {-sphi, cphi, 0.0};
+    double nsv[3] = {-szeta * cphi, -szeta * sphi, czeta};
+    // back to the ICRS: x_C = A' x_S
+    const double* e = (kind == 0) ? ms : nsv;
+    double ec[3] = {Am[0] * e[0] + Am[3] * e[1] + Am[6] * e[2], Am[1] * e[0] + Am[4] * e[1] + Am[7] * e[2],
+                    Am[2] * e[0] + Am[5] * e[1] + Am[8] * e[2]};
+    // du/ds' = [(1 - ub'v/c) I - ub v'/c] dub/ds'  (Eq. duds); e'du = (1-ubv) e'x - (e'ub)(v'x)
+    double ubv = dot3(ub, vc);
+    double eub = dot3(ec, ub);
+    double dpar[3] = {-(b[0] - S.r[0] * rb), -(b[1] - S.r[1] * rb), -(b[2] - S.r[2] * rb)};
+    double sc = (kind == 0) ? 1.0 / czeta : 1.0;
+    double Ap = ((1.0 - ubv) * dot3(ec, S.p) - eub * dot3(vc, S.p)) * sc;
+    double Aq = ((1.0 - ubv) * dot3(ec, S.q) - eub * dot3(vc, S.q)) * sc;
+    double Aw = ((1.0 - ubv) * dot3(ec, dpar) - eub * dot3(vc, dpar)) * sc;
+    o.A[0] = Ap; o.A[1] = Aq; o.A[2] = Aw; o.A[3] = Ap * tau; o.A[4] = Aq * tau;
+    // attitude: dR_AL/dq = 2 sec(zeta) q {n,0};  dR_AC/dq = -2 q {m,0}
+    double v4[4];
+    double gq[4];
+    if (kind == 0) {
+        v4[0] = nsv[0]; v4[1] = nsv[1]; v4[2] = nsv[2]; v4[3] = 0.0;
+        qmul(q, v4, gq);
+        double k2 = 2.0 / czeta / ns;
+        o.g[0] = gq[0] * k2; o.g[1] = gq[1] * k2; o.g[2] = gq[2] * k2; o.g[3] = gq[3] * k2;
+    } else {
+        v4[0] = ms[0]; v4[1] = ms[1]; v4[2] = ms[2]; v4[3] = 0.0;
+        qmul(q, v4, gq);
+        double k2 = -2.0 / ns;
+        o.g[0] = gq[0] * k2; o.g[1] = gq[1] * k2; o.g[2] = gq[2] * k2; o.g[3] = gq[3] * k2;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// 5x5 robust Cholesky (Algorithms C.1-C.3) in registers; N upper-packed row-major:
+// (0,0) (0,1) .. (0,4) (1,1) .. (1,4) (2,2) .. (4,4)
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int up5(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i); }
+
+__device__ __forceinline__ int chol5(const double* N, double* U, double tol) {
+    int d = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+#pragma unroll
+        for (int i = 0; i <= j; i++) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < i; k++) s += U[up5(k, i)] * U[up5(k, j)];
+            if (i < j) {
+                double uii = U[up5(i, i)];
+                U[up5(i, j)] = uii > 0.0 ? (N[up5(i, j)] - s) / uii : 0.0;
+            } else {
+                double v = N[up5(j, j)] - s;
+                if (v > tol * N[up5(j, j)]) {
+                    U[up5(j, j)] = sqrt(v);
+                } else {
+                    U[up5(j, j)] = 0.0;
+                    d++;
+                }
+            }
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ void chol5_solve(const double* U, const double* b, double* x) {
+    double y[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        double s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) s -= U[up5(k, i)] * y[k];
+        y[i] = U[up5(i, i)] > 0.0 ? s / U[up5(i, i)] : 0.0;
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; i--) {
+        double s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) s -= U[up5(i, k)] * x[k];
+        x[i] = U[up5(i, i)] > 0.0 ? s / U[up5(i, i)] : 0.0;
+    }
+}
+
+}  // namespace agis

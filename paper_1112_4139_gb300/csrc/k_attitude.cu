@@ -1,0 +1,266 @@
+// k_attitude.cu -- the A block (Sect. 5.2): per-knot-interval partial normals from the
+// time-ordered observations, assembly of the banded normals of each overlapping segment,
+// and the segmented robust banded Cholesky (App. C restricted to the envelope).
+#include "agis_internal.cuh"
+
+namespace agis {
+
+// linear index of the upper entry (i <= j) of a 16x16 symmetric matrix
+__host__ __device__ constexpr int tri16(int i, int j) { return i * 16 - i * (i - 1) / 2 + (j - i); }
+// 4x4 symmetric upper storage
+__host__ __device__ constexpr int tri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
+
+constexpr int kStage = 18;  // staged per observation: B[4], M[10], r[4]
+
+// One warp per knot interval l (left index), iv = l - 3.  For each observation
+// dR/da = B (x) g and dD/da = -2 B (x) s (Eqs. dfadq, dDldan), so its contribution to the
+// 16x16 block of the interval is W (B B') (x) (g g' + 4 lambda^2 s s') (Eq. normAmod) and
+// to the right-hand side -W B (x) (R g [- 2 lambda^2 D s]).
+__global__ void __launch_bounds__(256) k_att_accum(DevGeo G, double lambda2, int rhs_norm,
+                                                   const uint32_t* __restrict__ perm_t,
+                                                   const int64_t* __restrict__ ivl_off, int n_iv,
+                                                   const ObsRec* __restrict__ rec, const double* __restrict__ att,
+                                                   double* __restrict__ blk) {
+    __shared__ double stage_all[8][kWarp * kStage];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    double* stg = stage_all[wib];
+    // this lane's outputs: o = lane + 32 k, k = 0..4 (o < 152)
+    int oi[5], oj[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        int o = lane + 32 * k;
+        oi[k] = -1; oj[k] = -1;
+        if (o < 136) {
+            int i = 0;
+            while (o >= tri16(i, 15) + 1) i++;
+            oi[k] = i;
+            oj[k] = i + (o - tri16(i, i));
+        } else if (o < kBlkVals) {
+            oi[k] = o - 136;
+            oj[k] = -1;
+        }
+    }
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int iv = blockIdx.x * (blockDim.x >> 5) + wib; iv < n_iv; iv += nwarps) {
+        const int l = iv + 3;
+        double a[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) a[k] = att[4 * (int64_t)(l - 3) + k];
+        double acc[5] = {0, 0, 0, 0, 0};
+        const int64_t beg = ivl_off[iv], end = ivl_off[iv + 1];
+        for (int64_t base = beg; base < end; base += kWarp) {
+            const int64_t j = base + lane;
+            double* st = stg + lane * kStage;
+            if (j < end) {
+                const ObsRec r = rec[perm_t[j]];
+                double B[4];
+                bspline4(G, r.t_ns, l, B);
+                double s[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
+                const double W = r.W;
+                const double l4 = 4.0 * lambda2;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+#pragma unroll
+                    for (int e = c; e < 4; e++) st[4 + tri4(c, e)] = W * (r.g[c] * r.g[e] + l4 * s[c] * s[e]);
+                }
+                double D = 1.0 - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    double v = r.R * r.g[c];
+                    if (rhs_norm) v -= 2.0 * lambda2 * D * s[c];
+                    st[14 + c] = W * v;
+                    st[c] = B[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < kStage; c++) st[c] = 0.0;
+            }
+            __syncwarp();
+            const int cnt = (int)((end - base) < kWarp ? (end - base) : kWarp);
+            for (int q = 0; q < cnt; q++) {
+                const double* sq = stg + q * kStage;
+#pragma unroll
+                for (int k = 0; k < 5; k++) {
+                    if (oi[k] < 0) continue;
+                    const int i = oi[k];
+                    if (oj[k] >= 0) {
+                        const int jj = oj[k];
+                        const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
+                        const int mi = ci <= cj ? tri4(ci, cj) : tri4(cj, ci);
+                        acc[k] += sq[bi] * sq[bj] * sq[4 + mi];
+                    } else {
+                        acc[k] -= sq[i >> 2] * sq[14 + (i & 3)];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            int o = lane + 32 * k;
+            if (o < kBlkVals) blk[(int64_t)iv * kBlkVals + o] = acc[k];
+        }
+    }
+}
+
+// Band of every segment in column layout: bandc[(row0 + c)*16 + k] = N[c-k][c] (k = 0..15)
+// and rhs[row0 + c], summed over the knot intervals of the segment only.
+__global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, const int32_t* __restrict__ seg_l,
+                               const int32_t* __restrict__ seg_n, const double* __restrict__ blk,
+                               double* __restrict__ bandc, double* __restrict__ rhs) {
+    const int64_t total = seg_row[n_seg] * 16;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t >> 4;
+        const int k = (int)(t & 15);
+        int lo = 0, hi = n_seg - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (seg_row[mid] <= row) lo = mid; else hi = mid - 1;
+        }
+        const int sg = lo;
+        const int c = (int)(row - seg_row[sg]);
+        const int l_lo = seg_l[2 * sg], l_hi = seg_l[2 * sg + 1];
+        const int n_lo = seg_n[2 * sg];
+        const int v = c - k;
+        double val = 0.0;
+        if (v >= 0) {
+            const int nc = n_lo + (c >> 2), cc = c & 3;
+            const int nv = n_lo + (v >> 2), cv = v & 3;
+            int lb = nc > nv ? nc : nv;
+            int le = (nc < nv ? nc : nv) + 3;
+            if (lb < l_lo) lb = l_lo;
+            if (le > l_hi) le = l_hi;
+            for (int l = lb; l <= le; l++) {
+                const int i = 4 * (nv - l + 3) + cv, j = 4 * (nc - l + 3) + cc;
+                val += blk[(int64_t)(l - 3) * kBlkVals + tri16(i, j)];
+            }
+        }
+        bandc[t] = val;
+        if (k == 0) {
+            const int nc = n_lo + (c >> 2), cc = c & 3;
+            double r = 0.0;
+            int lb = nc < l_lo ? l_lo : nc;
+            int le = nc + 3 > l_hi ? l_hi : nc + 3;
+            for (int l = lb; l <= le; l++) r += blk[(int64_t)(l - 3) * kBlkVals + 136 + 4 * (nc - l + 3) + cc];
+            rhs[row] = r;
+        }
+    }
+}
+
+// One warp per segment: right-looking robust Cholesky (Algorithm C.1 on the envelope) with
+// forward substitution (C.2) fused, then back substitution (C.3).  Lanes 0..15 hold the
+// 16 columns of the sliding window W[a][b] = N[r+a][r+b] (a <= b); the window moves one row
+// per step by a shuffle, and the column entering at lane 15 is read from the band.
+__global__ void __launch_bounds__(64) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
+                                                  const double* __restrict__ bandc, const double* __restrict__ rhs,
+                                                  double* __restrict__ urow, double* __restrict__ yv,
+                                                  double* __restrict__ x, double tol, int* __restrict__ seg_rd) {
+    const int lane = threadIdx.x & 31;
+    const int sg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (sg >= n_seg) return;
+    const int64_t base = seg_row[sg];
+    const int64_t n = seg_row[sg + 1] - base;
+    const int b = lane;
+    const bool act = b < 16;
+    double w[16];
+#pragma unroll
+    for (int a = 0; a < 16; a++) w[a] = (act && a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
+    double dg = (act && b < n) ? bandc[(base + b) * 16] : 0.0;
+    double z = (act && b < n) ? rhs[base + b] : 0.0;
+    int rd = 0;
+    for (int64_t r = 0; r < n; r++) {
+        const double piv = __shfl_sync(0xffffffffu, w[0], 0);
+        const double dg0 = __shfl_sync(0xffffffffu, dg, 0);
+        const double urr = piv > tol * dg0 ? sqrt(piv) : 0.0;
+        rd += urr == 0.0;
+        double myU = (b == 0) ? urr : (urr > 0.0 ? w[0] / urr : 0.0);
+        if (!act || r + b >= n) myU = (b == 0) ? urr : 0.0;
+        const double zr = __shfl_sync(0xffffffffu, z, 0);
+        const double yr = urr > 0.0 ? zr / urr : 0.0;
+        if (act) urow[(base + r) * 16 + b] = myU;
+        if (b == 0) yv[base + r] = yr;
+        if (b >= 1) z -= myU * yr;
+        // trailing update W[a][b] -= U[r][r+a] U[r][r+b], 1 <= a <= b
+#pragma unroll
+        for (int a = 1; a < 16; a++) {
+            const double ua = __shfl_sync(0xffffffffu, myU, a);
+            if (a <= b && act) w[a] -= ua * myU;
+        }
+        // move the window: W'[a][b] = W[a+1][b+1]
+#pragma unroll
+        for (int a = 0; a < 15; a++) w[a] = __shfl_down_sync(0xffffffffu, w[a + 1], 1);
+        w[15] = 0.0;
+        z = __shfl_down_sync(0xffffffffu, z, 1);
+        dg = __shfl_down_sync(0xffffffffu, dg, 1);
+        if (b == 15) {
+            const int64_t c = r + 16;
+            if (c < n) {
+#pragma unroll
+                for (int a = 0; a < 16; a++) w[a] = bandc[(base + c) * 16 + (15 - a)];
+                dg = bandc[(base + c) * 16];
+                z = rhs[base + c];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 16; a++) w[a] = 0.0;
+                dg = 0.0;
+                z = 0.0;
+            }
+        }
+    }
+    // back substitution: lane b holds x_{r+b} (b >= 1)
+    double xw = 0.0;
+    for (int64_t r = n - 1; r >= 0; r--) {
+        const double ur = act ? urow[(base + r) * 16 + b] : 0.0;
+        double part = (b >= 1 && act) ? ur * xw : 0.0;
+        part = warp_sum(part);
+        const double urr = __shfl_sync(0xffffffffu, ur, 0);
+        const double xr = urr > 0.0 ? (yv[base + r] - part) / urr : 0.0;
+        if (b == 0) x[base + r] = xr;
+        xw = __shfl_up_sync(0xffffffffu, xw, 1);
+        if (b == 1) xw = xr;
+    }
+    if (lane == 0) seg_rd[sg] = rd;
+}
+
+// a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per coefficient.
+__global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ seg_u, const int32_t* __restrict__ seg_n,
+                            const int64_t* __restrict__ seg_row, const double* __restrict__ x,
+                            double* __restrict__ att) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < n_coef; n += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_seg - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (seg_u[2 * mid] <= n) lo = mid; else hi = mid - 1;
+        }
+        const int sg = lo;
+        const int64_t r0 = seg_row[sg] + 4 * (int64_t)(n - seg_n[2 * sg]);
+#pragma unroll
+        for (int c = 0; c < 4; c++) att[4 * (int64_t)n + c] += x[r0 + c];
+    }
+}
+
+void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
+                      int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s) {
+    int warps = n_iv;
+    int blocks = (warps + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_att_accum<<<blocks, 256, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
+}
+
+void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
+                      const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
+                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, cudaStream_t s) {
+    int64_t total = n_rows * 16;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_att_assemble<<<blocks, 256, 0, s>>>(n_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
+    k_att_solve<<<(n_seg + 1) / 2, 64, 0, s>>>(n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
+    k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att);
+}
+
+}  // namespace agis

@@ -1,0 +1,340 @@
+// k_source.cu -- the observation pass in source order and the S block (Sect. 5.1).
+//
+// One warp per source (persistent warps take sources from a work counter, largest first).
+// The warp evaluates every observation of the source once (residual h_l, design row A_l,
+// attitude partial g_l), keeps (h, A, w, sigma^2) in a per-warp scratch slice that stays in
+// L2 during the inner iteration, and runs the inner iteration of Sect. 5.1.2 with
+// butterfly (xor-shuffle) reductions, so every lane holds the same 5x5 system and solves it
+// redundantly.  At the end it writes the hand-over record (t, R = h - A d, W, g, meta) that
+// the time-ordered attitude pass and the calibration pass gather.
+#include "agis_internal.cuh"
+
+namespace agis {
+
+
+__device__ __forceinline__ uint64_t dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b < 0 ? ~(uint64_t)b : ((uint64_t)b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(uint64_t k) {
+    long long b = (k & 0x8000000000000000ull) ? (long long)(k & 0x7fffffffffffffffull) : (long long)(~k);
+    return __longlong_as_double(b);
+}
+
+// k-th smallest (0-based) of the keys stored in scr[j*kScr + 6] (as bit patterns), j < n,
+// by an 8-pass radix select with a 256-bin shared-memory histogram per warp.
+__device__ uint64_t warp_select(const double* scr, int n, int k, int* hist, int lane) {
+    uint64_t prefix = 0, pmask = 0;
+    int kk = k;
+    for (int d = 7; d >= 0; d--) {
+        int shift = 8 * d;
+#pragma unroll
+        for (int i = 0; i < 8; i++) hist[lane * 8 + i] = 0;
+        __syncwarp();
+        for (int j = lane; j < n; j += kWarp) {
+            uint64_t key = (uint64_t)__double_as_longlong(scr[(size_t)j * kScr + 6]);
+            if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+        }
+        __syncwarp();
+        int c[8];
+        int tot = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) { c[i] = hist[lane * 8 + i]; tot += c[i]; }
+        // inclusive scan across lanes
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int excl = incl - tot;
+        unsigned ball = __ballot_sync(0xffffffffu, incl > kk);
+        int src_lane = __ffs(ball) - 1;
+        int bin = 0, below = 0;
+        if (lane == src_lane) {
+            int acc = excl;
+            int bsel = 7;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                if (acc + c[i] > kk) { bsel = i; break; }
+                acc += c[i];
+            }
+            bin = lane * 8 + bsel;
+            below = acc;
+        }
+        bin = __shfl_sync(0xffffffffu, bin, src_lane);
+        below = __shfl_sync(0xffffffffu, below, src_lane);
+        kk -= below;
+        prefix |= (uint64_t)bin << shift;
+        pmask |= (uint64_t)0xffu << shift;
+        __syncwarp();
+    }
+    return prefix;
+}
+
+// the (k)-th and (k+1)-th smallest values (k+1 capped at n-1)
+__device__ void warp_select_pair(const double* scr, int n, int k, int* hist, int lane, double& v0, double& v1) {
+    uint64_t K = warp_select(scr, n, k, hist, lane);
+    v0 = dkey_inv(K);
+    if (k + 1 >= n) { v1 = v0; return; }
+    int less = 0, eq = 0;
+    uint64_t nxt = ~0ull;
+    for (int j = lane; j < n; j += kWarp) {
+        uint64_t key = (uint64_t)__double_as_longlong(scr[(size_t)j * kScr + 6]);
+        less += key < K;
+        eq += key == K;
+        if (key > K && key < nxt) nxt = key;
+    }
+    less = warp_sum_int(less);
+    eq = warp_sum_int(eq);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t v = __shfl_xor_sync(0xffffffffu, nxt, o);
+        nxt = v < nxt ? v : nxt;
+    }
+    v1 = (k + 1 < less + eq) ? v0 : dkey_inv(nxt);
+}
+
+struct Sys5 {
+    double N[15];
+    double b[5];
+};
+
+// normal equations with W = w / (sigma^2 + y); optionally refresh w from the previous solve
+__device__ __forceinline__ void pass_normals(double* scr, int n, int lane, double y, bool refresh, const double* dp,
+                                             double yp, int wfn, Sys5& S, int& nout) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) S.N[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 5; i++) S.b[i] = 0.0;
+    int cnt = 0;
+    for (int j = lane; j < n; j += kWarp) {
+        double* e = scr + (size_t)j * kScr;
+        double h = e[0];
+        double A[5] = {e[1], e[2], e[3], e[4], e[5]};
+        double w = e[6];
+        double s2 = e[7];
+        if (refresh) {
+            double R = h - (A[0] * dp[0] + A[1] * dp[1] + A[2] * dp[2] + A[3] * dp[3] + A[4] * dp[4]);
+            w = wfun(R / sqrt(s2 + yp), wfn);
+            e[6] = w;
+        }
+        cnt += (w < 0.2);
+        double W = w / (s2 + y);
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+            double wa = W * A[a];
+#pragma unroll
+            for (int c = a; c < 5; c++) S.N[up5(a, c)] += wa * A[c];
+            S.b[a] += wa * h;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 15; i++) S.N[i] = warp_sum(S.N[i]);
+#pragma unroll
+    for (int i = 0; i < 5; i++) S.b[i] = warp_sum(S.b[i]);
+    nout = warp_sum_int(cnt);
+}
+
+// Q(y) = sum w R^2 / (s2 + y) and S2 = sum w R^2 / (s2 + y)^2 for R = h - A d
+__device__ __forceinline__ void pass_q(const double* scr, int n, int lane, const double* d, double y, double& Q,
+                                       double& S2) {
+    double q = 0.0, s = 0.0;
+    for (int j = lane; j < n; j += kWarp) {
+        const double* e = scr + (size_t)j * kScr;
+        double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
+        double den = e[7] + y;
+        double t = e[6] * R * R / den;
+        q += t;
+        s += t / den;
+    }
+    Q = warp_sum(q);
+    S2 = warp_sum(s);
+}
+
+__global__ void __launch_bounds__(128) k_source_update(
+    DevGeo G, Settings st, const int64_t* __restrict__ t_ns, const uint32_t* __restrict__ meta,
+    const float* __restrict__ sigma, const double* __restrict__ mu, const int64_t* __restrict__ src_off,
+    const int32_t* __restrict__ src_order, int32_t n_src, const double* __restrict__ att,
+    const double* __restrict__ cal, SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch,
+    int cap, int* work_counter) {
+    __shared__ int hist_all[4 * 256];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int* hist = hist_all + wib * 256;
+    const size_t gw = (size_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    double* scr = scratch + gw * (size_t)cap * kScr;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(work_counter, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= n_src) break;
+        const int i = src_order[idx];
+        const int64_t o0 = src_off[i];
+        const int n = (int)(src_off[i + 1] - o0);
+        double s5[5];
+#pragma unroll
+        for (int k = 0; k < 5; k++) s5[k] = out.src[5 * (size_t)i + k];
+        if (n == 0) {
+            if (lane == 0) {
+                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = 0.0;
+                for (int k = 0; k < 25; k++) out.cov[25 * (size_t)i + k] = 0.0;
+                out.eps2[i] = out.q[i] = out.dsig[i] = out.chi2[i] = 0.0;
+                out.nu[i] = out.nout[i] = out.rankdef[i] = 0;
+            }
+            continue;
+        }
+        SrcGeo S;
+        source_geo(s5, S);
+        // ---- observation pass: residuals and partials at the current parameters
+        double s2min = 1e300;
+        for (int j = lane; j < n; j += kWarp) {
+            const int64_t o = o0 + j;
+            const int64_t t = t_ns[o];
+            const uint32_t m = meta[o];
+            const double muv = meta_kind(m) ? mu[o] : 0.0;
+            ObsOut ob;
+            observe<true>(G, S, t, m, muv, att, cal, ob);
+            const double sg = (double)sigma[o];
+            const double s2 = sg * sg;
+            double* e = scr + (size_t)j * kScr;
+            e[0] = ob.R;
+            e[1] = ob.A[0]; e[2] = ob.A[1]; e[3] = ob.A[2]; e[4] = ob.A[3]; e[5] = ob.A[4];
+            e[6] = __longlong_as_double((long long)dkey(ob.R / sg));
+            e[7] = s2;
+            ObsRec* r = rec + o;
+            r->t_ns = t;
+            r->meta = m;
+            r->pad = 0;
+            r->g[0] = ob.g[0]; r->g[1] = ob.g[1]; r->g[2] = ob.g[2]; r->g[3] = ob.g[3];
+            s2min = fmin(s2min, s2);
+        }
+        s2min = warp_min(s2min);
+        __syncwarp();
+        // ---- initial downweighting from the robust sigma (half the intersextile range)
+        if (st.robust) {
+            const double p1 = 1.0 / 6.0, p5 = 5.0 / 6.0;
+            double h1 = p1 * (double)(n - 1), h5 = p5 * (double)(n - 1);
+            int lo1 = (int)floor(h1), lo5 = (int)floor(h5);
+            double a0, a1, b0, b1;
+            warp_select_pair(scr, n, lo1, hist, lane, a0, a1);
+            warp_select_pair(scr, n, lo5, hist, lane, b0, b1);
+            double q1 = a0 + (h1 - lo1) * (a1 - a0);
+            double q5 = b0 + (h5 - lo5) * (b1 - b0);
+            double vs = 0.5 * (q5 - q1);
+            __syncwarp();
+            for (int j = lane; j < n; j += kWarp) {
+                double* e = scr + (size_t)j * kScr;
+                double x = e[0] / sqrt(e[7]);
+                e[6] = vs > 0.0 ? wfun(x / vs, st.weight_fn) : 1.0;
+            }
+        } else {
+            for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
+        }
+        __syncwarp();
+        // ---- inner iteration (Sect. 5.1.2)
+        double d[5] = {0, 0, 0, 0, 0};
+        double U[15];
+        double y = 0.0, Q = 0.0, Q0 = 0.0;
+        int nu = 0, nout = 0, rd = 0;
+        const int rounds = st.robust ? st.n_rounds + 1 : 1;
+        for (int rnd = 0; rnd < rounds; rnd++) {
+            Sys5 sy;
+            double dprev[5] = {d[0], d[1], d[2], d[3], d[4]};
+            const double yprev = y;
+            y = 0.0;
+            pass_normals(scr, n, lane, 0.0, rnd > 0, dprev, yprev, st.weight_fn, sy, nout);
+            nu = n - nout - 5;
+            rd = chol5(sy.N, U, st.pivot_tol);
+            chol5_solve(U, sy.b, d);
+            double S2;
+            pass_q(scr, n, lane, d, 0.0, Q, S2);
+            Q0 = Q;
+            if (st.robust && nu > 0 && Q0 > (double)nu) {
+                const double tol = 1e-12 * s2min;
+                for (int it = 0; it < st.n_eps; it++) {
+                    double dy = (1.0 - Q / (double)nu) * Q / (-S2);
+                    y = fmax(0.0, y + dy);
+                    pass_normals(scr, n, lane, y, false, dprev, yprev, st.weight_fn, sy, nout);
+                    rd = chol5(sy.N, U, st.pivot_tol);
+                    chol5_solve(U, sy.b, d);
+                    pass_q(scr, n, lane, d, y, Q, S2);
+                    if (fabs(dy) <= tol) break;
+                }
+            }
+            __syncwarp();
+        }
+        // ---- hand-over records: R = h - A d, W = w / (sigma^2 + eps^2)
+        double chi = 0.0;
+        for (int j = lane; j < n; j += kWarp) {
+            const double* e = scr + (size_t)j * kScr;
+            double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
+            double W = e[6] / (e[7] + y);
+            ObsRec* r = rec + (o0 + j);
+            r->R = R;
+            r->W = W;
+            chi += W * R * R;
+        }
+        chi = warp_sum(chi);
+        // ---- per-source results (lane 0); covariance from the last factor (App. C.2)
+        if (lane == 0) {
+            double* sp = out.src + 5 * (size_t)i;
+            sp[0] = s5[0] + d[0] / S.cosd;
+            sp[1] = s5[1] + d[1];
+            sp[2] = s5[2] + d[2];
+            sp[3] = s5[3] + d[3];
+            sp[4] = s5[4] + d[4];
+            for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
+            for (int c = 0; c < 5; c++) {
+                double e[5] = {0, 0, 0, 0, 0};
+                e[c] = 1.0;
+                double x[5];
+                chol5_solve(U, e, x);
+                for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
+            }
+            out.eps2[i] = y;
+            out.q[i] = Q;
+            out.nu[i] = nu;
+            out.nout[i] = nout;
+            out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
+            out.chi2[i] = chi;
+            out.rankdef[i] = rd;
+        }
+        __syncwarp();
+    }
+}
+
+// Residuals at the current parameters, one thread per observation (no update).
+__global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uint32_t* __restrict__ meta,
+                           const double* __restrict__ mu, const int32_t* __restrict__ obs_src, int64_t n_obs,
+                           const double* __restrict__ src, const double* __restrict__ att,
+                           const double* __restrict__ cal, double* __restrict__ R) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
+        SrcGeo S;
+        source_geo(src + 5 * (size_t)obs_src[o], S);
+        uint32_t m = meta[o];
+        ObsOut ob;
+        observe<false>(G, S, t_ns[o], m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
+        R[o] = ob.R;
+    }
+}
+
+void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_ns, const uint32_t* meta,
+                          const float* sigma, const double* mu, const int64_t* src_off, const int32_t* src_order,
+                          int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out, ObsRec* rec,
+                          double* scratch, int cap, int* work_counter, int n_blocks, cudaStream_t stream) {
+    cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
+    k_source_update<<<n_blocks, 128, 0, stream>>>(G, st, t_ns, meta, sigma, mu, src_off, src_order, n_src, att,
+                                                  cal, out, rec, scratch, cap, work_counter);
+}
+
+void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
+                     const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
+                     double* R, cudaStream_t stream) {
+    int blocks = (int)((n_obs + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_evaluate<<<blocks, 256, 0, stream>>>(G, t_ns, meta, mu, obs_src, n_obs, src, att, cal, R);
+}
+
+}  // namespace agis

@@ -1,0 +1,32 @@
+"""The C-ABI library loads and exports every symbol that include/agis.h declares (no GPU needed)."""
+import os
+import re
+
+import paper_1112_4139_gb300 as pkg
+from paper_1112_4139_gb300 import agis
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "agis.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(agis_[a-z_0-9]+)\s*\(", src))
+
+
+def test_library_builds_and_exports_all_declared_symbols():
+    path = pkg.build()
+    assert os.path.exists(path)
+    lib = agis.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    assert declared == set(agis.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert lib.agis_abi_version() == 1
+
+
+def test_default_config_and_struct_sizes():
+    cfg = agis.default_config()
+    assert cfg.robust == 1 and cfg.n_rounds == 4 and cfg.n_eps == 3 and abs(cfg.lambda_att - 1e-3) < 1e-18
+    assert cfg.seg_overlap == 12 and cfg.pivot_tol == 1e-12
