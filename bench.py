@@ -274,7 +274,7 @@ def main():
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t)
         ge.close()
-    e2e = world * ds.n_obs / float(np.median(e2e_times))
+    e2e = world * ds.n_obs / float(np.median(e2e_times)) if e2e_times else None
     peaks = load_peaks()
     # FP64 arithmetic bound: the S pass is limited by the FP64 pipe (the design doc derives the
     # peak from the FP64 unit count and clock: 1.25 TFLOP/s nominal for GB300)
@@ -289,7 +289,8 @@ def main():
                    "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "t_generate_s": round(t_gen, 1), "t_init_s": round(t_init, 2)},
-        "e2e": {"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": ({"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+                if e2e is not None else None),
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "kernel": "k_source_update (S pass, FP64)", "achieved": achieved,

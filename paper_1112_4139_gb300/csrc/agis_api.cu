@@ -209,9 +209,9 @@ struct agis_ctx {
     bool have_s = false;
     cudaEvent_t ev[12];
     double ktimes[5] = {0, 0, 0, 0, 0};
-    cudaGraphExec_t graph_exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    int graph_frame = -1;
+    cudaGraphExec_t graph_execs[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
 };
@@ -298,7 +298,10 @@ void build_segments(int n_coef, int seg_len, int L, std::vector<int32_t>& sl, st
 void record(agis_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
 double elapsed(agis_ctx* c, int a, int b) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]);
+    if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1.0;
+    }
     return ms;
 }
 
@@ -370,8 +373,10 @@ const char* agis_last_error(const agis_ctx* ctx) { return ctx ? ctx->err.c_str()
 void agis_destroy(agis_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    for (int b = 0; b < 4; b++) {
+        if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
+        if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
+    }
     for (void* p : c->allocs) cudaFree(p);
     if (c->hstat) cudaFreeHost(c->hstat);
     if (c->hisum) cudaFreeHost(c->hisum);
@@ -699,57 +704,62 @@ int agis_frame_rotate(agis_ctx* c, const int32_t* subset, int32_t n_subset, doub
 int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t* n_done) {
     if (!c) return AGIS_E_INVALID;
     if (n_done) *n_done = 0;
+    if (n_iter < 0) return fail(c, AGIS_E_INVALID, "negative iteration count");
     const bool do_frame = c->cfg.frame_each_iter && c->ref;
     const int mask = c->cfg.block_mask;
-    auto enqueue_iter = [&]() {
-        record(c, 8);
-        if (mask & 1) enqueue_s(c);
-        record(c, 9);
-        if (mask & 2) enqueue_a(c);
-        record(c, 10);
-        if (mask & 4) enqueue_c(c);
-        if (do_frame) enqueue_frame(c, nullptr, c->n_src);
-        record(c, 11);
-        cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(c->hisum, c->isum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
-        if (do_frame) cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    };
     if (!(mask & 1) && (mask & 6) && !c->have_s)
         return fail(c, AGIS_E_INVALID, "A/C blocks without an S block need a prior source update");
-    cudaMemsetAsync(c->isum, 0, 2 * sizeof(long long), c->stream);
     const bool graph = c->cfg.use_graph != 0;
-    if (graph && c->graph_exec && c->graph_frame != (int)do_frame) {
-        cudaGraphExecDestroy(c->graph_exec);
-        cudaGraphDestroy(c->graph);
-        c->graph_exec = nullptr;
-        c->graph = nullptr;
-    }
-    if (graph && !c->graph_exec) {
-        AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        enqueue_iter();
-        AGIS_CU(c, cudaStreamEndCapture(c->stream, &c->graph), "end capture");
-        AGIS_CU(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0), "instantiate graph");
-        c->graph_frame = (int)do_frame;
-    }
-    for (int32_t k = 0; k < n_iter; k++) {
-        if (graph) {
-            AGIS_CU(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
-        } else {
-            enqueue_iter();
+    // one graph per block, so that the blocks can be timed by events between the launches
+    if (graph && !c->graphs_ready) {
+        for (int b = 0; b < 4; b++) {
+            AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            if (b == 0) enqueue_s(c);
+            if (b == 1) enqueue_a(c);
+            if (b == 2) enqueue_c(c);
+            if (b == 3 && c->ref) enqueue_frame(c, nullptr, c->n_src);
+            AGIS_CU(c, cudaStreamEndCapture(c->stream, &c->graphs[b]), "end capture");
+            AGIS_CU(c, cudaGraphInstantiate(&c->graph_execs[b], c->graphs[b], 0), "instantiate graph");
         }
+        c->graphs_ready = true;
+    }
+    auto run_block = [&](int b) -> int {
+        if (graph) return cuda_check(c, cudaGraphLaunch(c->graph_execs[b], c->stream), "graph launch");
+        if (b == 0) enqueue_s(c);
+        if (b == 1) enqueue_a(c);
+        if (b == 2) enqueue_c(c);
+        if (b == 3) enqueue_frame(c, nullptr, c->n_src);
+        return cuda_check(c, cudaGetLastError(), "block launch");
+    };
+    for (int32_t k = 0; k < n_iter; k++) {
+        AGIS_CU(c, cudaEventRecord(c->ev[8], c->stream), "event");
+        if (mask & 1) AGIS_TRY(run_block(0));
+        AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
+        if (mask & 2) AGIS_TRY(run_block(1));
+        AGIS_CU(c, cudaEventRecord(c->ev[10], c->stream), "event");
+        if (mask & 4) AGIS_TRY(run_block(2));
+        if (do_frame) AGIS_TRY(run_block(3));
+        AGIS_CU(c, cudaEventRecord(c->ev[11], c->stream), "event");
+        AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                "stats");
+        AGIS_CU(c, cudaMemcpyAsync(c->hisum, c->isum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream),
+                "stats");
+        if (do_frame)
+            AGIS_CU(c, cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                    "stats");
         AGIS_CU(c, cudaStreamSynchronize(c->stream), "iteration");
-        AGIS_CU(c, cudaGetLastError(), "iteration kernels");
         if (mask & 1) c->have_s = !do_frame;
         if (per_iter) {
             agis_iter_stats& it = per_iter[k];
             std::memset(&it, 0, sizeof(it));
             if (mask & 1) fill_s_stats(c, c->hstat, &it.s);
-            it.a.rank_defect = c->hisum[0];
-            it.c.rank_defect = c->hisum[1];
+            it.a.rank_defect = (mask & 2) ? c->hisum[0] : 0;
+            it.c.rank_defect = (mask & 4) ? c->hisum[1] : 0;
             if (do_frame)
                 for (int i = 0; i < 6; i++) it.frame[i] = c->hstat[16 + i];
             it.s.elapsed_ms = elapsed(c, 8, 9);
             it.a.elapsed_ms = elapsed(c, 9, 10);
+            it.c.elapsed_ms = elapsed(c, 10, 11);
             it.elapsed_ms = elapsed(c, 8, 11);
         }
         if ((mask & 1) && !std::isfinite(c->hstat[0])) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2");

@@ -19,8 +19,13 @@ UAS = synth.UAS
 TOL_SRC = 0.5 * UAS
 
 
-def _r_ok(Rg, Rc):
-    return np.abs(Rg - Rc) <= 1e-9 * np.abs(Rc) + 1e-15
+def _r_ok(Rg, Rc, floor=1e-15):
+    return np.abs(Rg - Rc) <= 1e-9 * np.abs(Rc) + floor
+
+
+# residuals after a source update, R = h - A d, inherit the rounding of the solved d: their
+# floor is the source-parameter tolerance times |A| ~ 1 instead of the fixed-parameter 1e-15
+R_AFTER_S_FLOOR = 1e-3 * UAS
 
 
 @pytest.fixture(scope="module")
@@ -74,7 +79,7 @@ def _compare_source_block(lib, ds, st, **cfg):
     e = OG.source_errors(sg, src1)
     assert np.max(np.abs(e)) < TOL_SRC, f"max source diff {np.max(np.abs(e)) / UAS:.3e} uas"
     Rg, Wg = g.residuals()
-    assert _r_ok(Rg, sres.R).all(), f"R after S: max diff {np.abs(Rg - sres.R).max():.3e}"
+    assert _r_ok(Rg, sres.R, R_AFTER_S_FLOOR).all(), f"R after S: max diff {np.abs(Rg - sres.R).max():.3e}"
     assert np.allclose(Wg, sres.W, rtol=1e-9, atol=0)
     ss = g.source_stats()
     assert np.array_equal(ss["nu"].astype(int), sres.nu)
@@ -178,7 +183,7 @@ def test_two_iterations(lib, data, use_graph):
 
 def test_edge_cases_empty_and_short_sources(lib):
     # sources without observations and with fewer than 5 observations (singular 5x5)
-    ds = synth.simulate(synth.config("small1yr", n_src=400, seed=5))
+    ds = synth.simulate(synth.config("small1yr", n_src=600, seed=5, min_transits=10))
     keep = np.ones(ds.n_obs, bool)
     first = ds.src_offsets()
     keep[first[7] + 3:first[8]] = False       # source 7: 3 observations
