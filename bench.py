@@ -28,10 +28,11 @@ WORKLOADS = {
     "scale5yr": "1M sources, 5 yr, 30-s knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
     "small1yr": "10k sources, 1 yr, 1-h knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
 }
-# kernels launched by one iteration: S (source update, stats), A (accumulate, assemble,
+# kernels launched by one iteration: S (source geometry, observation pass, per-source solve,
+# stats), A (accumulate, assemble,
 # solve, apply, rank-defect sum), C (accumulate, project, rank-defect sum), frame (normals,
 # solve, apply sources, apply attitude)
-KERNELS_PER_STEP = 14
+KERNELS_PER_STEP = 16
 
 
 def parse():
@@ -293,7 +294,7 @@ def main():
                 if e2e is not None else None),
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": "k_source_update (S pass, FP64)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_obs_forward + k_source_solve (S pass, FP64)", "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock), not in MEASURED_PEAKS.json",
                      "flops_per_obs": S_FLOPS_PER_OBS},

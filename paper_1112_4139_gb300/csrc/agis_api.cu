@@ -13,9 +13,10 @@
 
 namespace agis {
 void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_ns, const uint32_t* meta,
-                          const float* sigma, const double* mu, const int64_t* src_off, const int32_t* src_order,
-                          int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out, ObsRec* rec,
-                          double* scratch, int cap, int* work_counter, int n_blocks, cudaStream_t stream);
+                          const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs,
+                          const int64_t* src_off, const int32_t* src_order, int32_t n_src, const double* att,
+                          const double* cal, const SrcOutPtrs& out, ObsRec* rec, double* geo, double* scratch,
+                          int* work_counter, int n_blocks, cudaStream_t stream);
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
@@ -172,7 +173,8 @@ struct agis_ctx {
     double* cal = nullptr;
     // S block
     ObsRec* rec = nullptr;
-    double* scratch = nullptr;
+    double* scratch = nullptr;   // n_obs x 8 doubles, source order
+    double* sgeo = nullptr;      // n_src x 16
     int cap = 0, n_sblocks = 0;
     int* work = nullptr;
     SrcOutPtrs so{};
@@ -307,8 +309,9 @@ double elapsed(agis_ctx* c, int a, int b) {
 
 // --- the block sequences (enqueue only; no host synchronisation) ---------------------------
 void enqueue_s(agis_ctx* c) {
-    launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->src_off, c->src_order, c->n_src, c->att,
-                         c->cal, c->so, c->rec, c->scratch, c->cap, c->work, c->n_sblocks, c->stream);
+    launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
+                         c->src_order, c->n_src, c->att, c->cal, c->so, c->rec, c->sgeo, c->scratch, c->work,
+                         c->n_sblocks, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
 }
@@ -546,17 +549,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         if (n_src > 0 && (rc = sort_pairs(c, k_in, k_out, (uint32_t*)i_in, (uint32_t*)c->src_order, n_src, 32)))
             return bail(rc);
     }
-    c->n_sblocks = c->n_sm * 4;
-    {
-        size_t want = (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr * sizeof(double);
-        const size_t limit = (size_t)8 << 30;
-        while (want > limit && c->n_sblocks > c->n_sm) {
-            c->n_sblocks /= 2;
-            want = (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr * sizeof(double);
-        }
-    }
+    c->n_sblocks = c->n_sm * 8;
     if ((rc = dalloc(c, &c->rec, n)) ||
-        (rc = dalloc(c, &c->scratch, (size_t)c->n_sblocks * 4 * (size_t)c->cap * kScr)) ||
+        (rc = dalloc(c, &c->scratch, (size_t)n * kScr)) || (rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
         (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
         (rc = dalloc(c, &c->so.eps2, n_src)) || (rc = dalloc(c, &c->so.q, n_src)) ||
         (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||

@@ -152,18 +152,164 @@ __device__ __forceinline__ void pass_q(const double* scr, int n, int lane, const
     S2 = warp_sum(s);
 }
 
-__global__ void __launch_bounds__(128) k_source_update(
-    DevGeo G, Settings st, const int64_t* __restrict__ t_ns, const uint32_t* __restrict__ meta,
-    const float* __restrict__ sigma, const double* __restrict__ mu, const int64_t* __restrict__ src_off,
-    const int32_t* __restrict__ src_order, int32_t n_src, const double* __restrict__ att,
-    const double* __restrict__ cal, SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch,
-    int cap, int* work_counter) {
+// ---- per-class sums: when every AL observation of a source has one sigma and every AC
+// observation another, N(y) = sum_c AA_c / (s2_c + y), b(y) = sum_c Ah_c / (s2_c + y) and
+// Q(y) = sum_c [hh_c - 2 d'Ah_c + d'AA_c d] / (s2_c + y): one pass over the observations per
+// weight round serves every excess-noise step (exact algebra; only the rounding differs).
+struct ClassSums {
+    double AA[2][15];
+    double Ah[2][5];
+    double hh[2];
+};
+
+// Sums of one class.  mode 0: w = wfun(x / vs) with x = h / sigma (initial downweighting);
+// mode 1: refresh w = wfun(R / sqrt(s2 + y_prev)) with R = h - A d_prev; mode 2: keep the stored
+// w.  The new w is stored in the scratch.  Each observation belongs to exactly one class, so
+// the two calls of a round visit every observation once.
+__device__ __forceinline__ void pass_class1(double* scr, int n, int lane, int cls, int mode, double vs, double sig,
+                                            const double* dp, double inv_sd, int wfn, double* AA, double* Ah,
+                                            double& hh, int& nout) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) AA[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 5; i++) Ah[i] = 0.0;
+    double hs = 0.0;
+    int cnt = 0;
+    for (int j = lane; j < n; j += kWarp) {
+        double* e = scr + (size_t)j * kScr;
+        if ((e[7] != 0.0 ? 1 : 0) != cls) continue;
+        const double h = e[0];
+        const double A[5] = {e[1], e[2], e[3], e[4], e[5]};
+        double w;
+        if (mode == 0) {
+            const double x = h / sig;
+            w = vs > 0.0 ? wfun(x / vs, wfn) : 1.0;
+            e[6] = w;
+        } else if (mode == 1) {
+            const double R = h - (A[0] * dp[0] + A[1] * dp[1] + A[2] * dp[2] + A[3] * dp[3] + A[4] * dp[4]);
+            w = wfun(R * inv_sd, wfn);
+            e[6] = w;
+        } else {
+            w = e[6];
+        }
+        cnt += (w < 0.2);
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+            const double wa = w * A[a];
+#pragma unroll
+            for (int b = a; b < 5; b++) AA[up5(a, b)] += wa * A[b];
+            Ah[a] += wa * h;
+        }
+        hs += w * h * h;
+    }
+#pragma unroll
+    for (int i = 0; i < 15; i++) AA[i] = warp_sum(AA[i]);
+#pragma unroll
+    for (int i = 0; i < 5; i++) Ah[i] = warp_sum(Ah[i]);
+    hh = warp_sum(hs);
+    nout = warp_sum_int(cnt);
+}
+
+// both classes; the sums (identical in every lane after the butterflies) go to the warp's
+// shared-memory slot so that they do not occupy registers during the 5x5 algebra
+__device__ __forceinline__ void pass_class(double* scr, int n, int lane, int mode, double vs, const double* sig_c,
+                                           const double* dp, const double* inv_sd, int wfn, ClassSums& S,
+                                           int& nout) {
+    int nc[2];
+    for (int c = 0; c < 2; c++) {
+        double AA[15], Ah[5], hh;
+        pass_class1(scr, n, lane, c, mode, vs, sig_c[c], dp, inv_sd[c], wfn, AA, Ah, hh, nc[c]);
+        if (lane == 0) {
+            for (int i = 0; i < 15; i++) S.AA[c][i] = AA[i];
+            for (int i = 0; i < 5; i++) S.Ah[c][i] = Ah[i];
+            S.hh[c] = hh;
+        }
+    }
+    __syncwarp();
+    nout = nc[0] + nc[1];
+}
+
+// solve at excess variance y from the class sums; returns Q(y) and S2 = sum num_c/(s2_c+y)^2
+__device__ __noinline__ void class_solve(const ClassSums& S, const double* s2c, double y, double tol_piv,
+                                            double* U, double* d, int& rd, double& Q, double& S2) {
+    const double i0 = 1.0 / (s2c[0] + y), i1 = 1.0 / (s2c[1] + y);
+    double N[15], b[5];
+#pragma unroll
+    for (int i = 0; i < 15; i++) N[i] = S.AA[0][i] * i0 + S.AA[1][i] * i1;
+#pragma unroll
+    for (int i = 0; i < 5; i++) b[i] = S.Ah[0][i] * i0 + S.Ah[1][i] * i1;
+    rd = chol5(N, U, tol_piv);
+    chol5_solve(U, b, d);
+    double num[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        double dMd = 0.0, db = 0.0;
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+            db += d[a] * S.Ah[c][a];
+            dMd += S.AA[c][up5(a, a)] * d[a] * d[a];
+#pragma unroll
+            for (int k = a + 1; k < 5; k++) dMd += 2.0 * S.AA[c][up5(a, k)] * d[a] * d[k];
+        }
+        num[c] = S.hh[c] - 2.0 * db + dMd;
+    }
+    Q = num[0] * i0 + num[1] * i1;
+    S2 = num[0] * i0 * i0 + num[1] * i1 * i1;
+}
+
+// Per-source geometry for the observation pass: p, q, r (Eq. normal-triad), parameters, cos(delta).
+__global__ void k_src_geo(int32_t n_src, const double* __restrict__ src, double* __restrict__ geo) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        SrcGeo S;
+        source_geo(src + 5 * (size_t)i, S);
+        double* g = geo + 16 * (size_t)i;
+        for (int k = 0; k < 3; k++) { g[k] = S.p[k]; g[3 + k] = S.q[k]; g[6 + k] = S.r[k]; }
+        g[9] = S.par; g[10] = S.pma; g[11] = S.pmd; g[12] = S.cosd;
+    }
+}
+
+// Observation pass, one thread per observation (source order): residual h, design row A and
+// attitude partial g at the current parameters.  Scratch row: h, A[5], key(h/sigma), sigma^2.
+__global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, int64_t n_obs, const int64_t* __restrict__ t_ns,
+                                                     const uint32_t* __restrict__ meta,
+                                                     const float* __restrict__ sigma, const double* __restrict__ mu,
+                                                     const int32_t* __restrict__ obs_src,
+                                                     const double* __restrict__ geo, const double* __restrict__ att,
+                                                     const double* __restrict__ cal, double* __restrict__ scr,
+                                                     ObsRec* __restrict__ rec) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
+        const double* g = geo + 16 * (size_t)obs_src[o];
+        SrcGeo S;
+        for (int k = 0; k < 3; k++) { S.p[k] = g[k]; S.q[k] = g[3 + k]; S.r[k] = g[6 + k]; }
+        S.par = g[9]; S.pma = g[10]; S.pmd = g[11]; S.cosd = g[12];
+        const int64_t t = t_ns[o];
+        const uint32_t m = meta[o];
+        const double muv = meta_kind(m) ? mu[o] : 0.0;
+        ObsOut ob;
+        observe<true>(G, S, t, m, muv, att, cal, ob);
+        const double sg = (double)sigma[o];
+        double* e = scr + (size_t)o * kScr;
+        e[0] = ob.R;
+        e[1] = ob.A[0]; e[2] = ob.A[1]; e[3] = ob.A[2]; e[4] = ob.A[3]; e[5] = ob.A[4];
+        e[6] = __longlong_as_double((long long)dkey(ob.R / sg));
+        e[7] = sg * sg;
+        ObsRec* r = rec + o;
+        r->t_ns = t;
+        r->meta = m;
+        r->pad = 0;
+        r->g[0] = ob.g[0]; r->g[1] = ob.g[1]; r->g[2] = ob.g[2]; r->g[3] = ob.g[3];
+    }
+}
+
+__global__ void __launch_bounds__(128) k_source_solve(
+    Settings st, const uint32_t* __restrict__ meta, const int64_t* __restrict__ src_off,
+    const int32_t* __restrict__ src_order, int32_t n_src, SrcOutPtrs out, ObsRec* __restrict__ rec,
+    double* __restrict__ scratch, int* work_counter) {
     __shared__ int hist_all[4 * 256];
+    __shared__ ClassSums cls_all[4];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int* hist = hist_all + wib * 256;
-    const size_t gw = (size_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    double* scr = scratch + gw * (size_t)cap * kScr;
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(work_counter, 1);
@@ -184,34 +330,28 @@ __global__ void __launch_bounds__(128) k_source_update(
             }
             continue;
         }
-        SrcGeo S;
-        source_geo(s5, S);
-        // ---- observation pass: residuals and partials at the current parameters
+        const double cosd = cos(s5[1]);
+        double* scr = scratch + (size_t)o0 * kScr;
+        // ---- per-class sigma ranges of this source
         double s2min = 1e300;
+        double s2lo[2] = {1e300, 1e300}, s2hi[2] = {-1e300, -1e300};
         for (int j = lane; j < n; j += kWarp) {
-            const int64_t o = o0 + j;
-            const int64_t t = t_ns[o];
-            const uint32_t m = meta[o];
-            const double muv = meta_kind(m) ? mu[o] : 0.0;
-            ObsOut ob;
-            observe<true>(G, S, t, m, muv, att, cal, ob);
-            const double sg = (double)sigma[o];
-            const double s2 = sg * sg;
-            double* e = scr + (size_t)j * kScr;
-            e[0] = ob.R;
-            e[1] = ob.A[0]; e[2] = ob.A[1]; e[3] = ob.A[2]; e[4] = ob.A[3]; e[5] = ob.A[4];
-            e[6] = __longlong_as_double((long long)dkey(ob.R / sg));
-            e[7] = s2;
-            ObsRec* r = rec + o;
-            r->t_ns = t;
-            r->meta = m;
-            r->pad = 0;
-            r->g[0] = ob.g[0]; r->g[1] = ob.g[1]; r->g[2] = ob.g[2]; r->g[3] = ob.g[3];
+            const double s2 = scr[(size_t)j * kScr + 7];
+            const int c = meta_kind(meta[o0 + j]);
+            s2lo[c] = fmin(s2lo[c], s2);
+            s2hi[c] = fmax(s2hi[c], s2);
             s2min = fmin(s2min, s2);
         }
         s2min = warp_min(s2min);
+        for (int c = 0; c < 2; c++) {
+            s2lo[c] = warp_min(s2lo[c]);
+            s2hi[c] = -warp_min(-s2hi[c]);
+        }
+        // every AL observation with one sigma and every AC observation with one sigma
+        const bool classes = (s2lo[0] == s2hi[0] || s2lo[0] == 1e300) && (s2lo[1] == s2hi[1] || s2lo[1] == 1e300);
         __syncwarp();
-        // ---- initial downweighting from the robust sigma (half the intersextile range)
+        double vs = 0.0;
+        // ---- robust sigma (half the intersextile range of h / sigma)
         if (st.robust) {
             const double p1 = 1.0 / 6.0, p5 = 5.0 / 6.0;
             double h1 = p1 * (double)(n - 1), h5 = p5 * (double)(n - 1);
@@ -221,8 +361,89 @@ __global__ void __launch_bounds__(128) k_source_update(
             warp_select_pair(scr, n, lo5, hist, lane, b0, b1);
             double q1 = a0 + (h1 - lo1) * (a1 - a0);
             double q5 = b0 + (h5 - lo5) * (b1 - b0);
-            double vs = 0.5 * (q5 - q1);
+            vs = 0.5 * (q5 - q1);
             __syncwarp();
+        }
+        if (classes) {
+            // class-sum path: slot 7 holds the class (0 AL, 1 AC)
+            for (int j = lane; j < n; j += kWarp) {
+                const int64_t o = o0 + j;
+                scr[(size_t)j * kScr + 7] = (double)meta_kind(meta[o]);
+            }
+            __syncwarp();
+            double s2c[2] = {s2lo[0] == 1e300 ? 1.0 : s2lo[0], s2lo[1] == 1e300 ? 1.0 : s2lo[1]};
+            double sigc[2] = {sqrt(s2c[0]), sqrt(s2c[1])};
+            double d[5] = {0, 0, 0, 0, 0};
+            double U[15];
+            double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
+            int nu = 0, nout = 0, rd = 0;
+            const int rounds = st.robust ? st.n_rounds + 1 : 1;
+            ClassSums& cs = cls_all[wib];
+            for (int rnd = 0; rnd < rounds; rnd++) {
+                const double isd[2] = {1.0 / sqrt(s2c[0] + y), 1.0 / sqrt(s2c[1] + y)};
+                const double dprev[5] = {d[0], d[1], d[2], d[3], d[4]};
+                if (!st.robust) {
+                    for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
+                    __syncwarp();
+                    pass_class(scr, n, lane, 2, 0.0, sigc, dprev, isd, st.weight_fn, cs, nout);
+                } else {
+                    pass_class(scr, n, lane, rnd == 0 ? 0 : 1, vs, sigc, dprev, isd, st.weight_fn, cs, nout);
+                }
+                nu = n - nout - 5;
+                y = 0.0;
+                class_solve(cs, s2c, 0.0, st.pivot_tol, U, d, rd, Q, S2);
+                Q0 = Q;
+                if (st.robust && nu > 0 && Q0 > (double)nu) {
+                    const double tol = 1e-12 * s2min;
+                    for (int it = 0; it < st.n_eps; it++) {
+                        const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
+                        y = fmax(0.0, y + dy);
+                        class_solve(cs, s2c, y, st.pivot_tol, U, d, rd, Q, S2);
+                        if (fabs(dy) <= tol) break;
+                    }
+                }
+                __syncwarp();
+            }
+            const double iw[2] = {1.0 / (s2c[0] + y), 1.0 / (s2c[1] + y)};
+            double chi = 0.0;
+            for (int j = lane; j < n; j += kWarp) {
+                const double* e = scr + (size_t)j * kScr;
+                const double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
+                const double W = e[6] * iw[e[7] != 0.0 ? 1 : 0];
+                ObsRec* r = rec + (o0 + j);
+                r->R = R;
+                r->W = W;
+                chi += W * R * R;
+            }
+            chi = warp_sum(chi);
+            if (lane == 0) {
+                double* sp = out.src + 5 * (size_t)i;
+                sp[0] = s5[0] + d[0] / cosd;
+                sp[1] = s5[1] + d[1];
+                sp[2] = s5[2] + d[2];
+                sp[3] = s5[3] + d[3];
+                sp[4] = s5[4] + d[4];
+                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
+                for (int c = 0; c < 5; c++) {
+                    double e[5] = {0, 0, 0, 0, 0};
+                    e[c] = 1.0;
+                    double x[5];
+                    chol5_solve(U, e, x);
+                    for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
+                }
+                out.eps2[i] = y;
+                out.q[i] = Q;
+                out.nu[i] = nu;
+                out.nout[i] = nout;
+                out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
+                out.chi2[i] = chi;
+                out.rankdef[i] = rd;
+            }
+            __syncwarp();
+            continue;
+        }
+        // ---- general path: initial downweighting from the robust sigma
+        if (st.robust) {
             for (int j = lane; j < n; j += kWarp) {
                 double* e = scr + (size_t)j * kScr;
                 double x = e[0] / sqrt(e[7]);
@@ -279,7 +500,7 @@ __global__ void __launch_bounds__(128) k_source_update(
         // ---- per-source results (lane 0); covariance from the last factor (App. C.2)
         if (lane == 0) {
             double* sp = out.src + 5 * (size_t)i;
-            sp[0] = s5[0] + d[0] / S.cosd;
+            sp[0] = s5[0] + d[0] / cosd;
             sp[1] = s5[1] + d[1];
             sp[2] = s5[2] + d[2];
             sp[3] = s5[3] + d[3];
@@ -320,12 +541,18 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
 }
 
 void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_ns, const uint32_t* meta,
-                          const float* sigma, const double* mu, const int64_t* src_off, const int32_t* src_order,
-                          int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out, ObsRec* rec,
-                          double* scratch, int cap, int* work_counter, int n_blocks, cudaStream_t stream) {
+                          const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs,
+                          const int64_t* src_off, const int32_t* src_order, int32_t n_src, const double* att,
+                          const double* cal, const SrcOutPtrs& out, ObsRec* rec, double* geo, double* scratch,
+                          int* work_counter, int n_blocks, cudaStream_t stream) {
+    k_src_geo<<<(n_src + 255) / 256 > 0 ? (n_src + 255) / 256 : 1, 256, 0, stream>>>(n_src, out.src, geo);
+    int fb = (int)((n_obs + 255) / 256);
+    if (fb > 152 * 64) fb = 152 * 64;
+    if (fb < 1) fb = 1;
+    k_obs_forward<<<fb, 256, 0, stream>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
     cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
-    k_source_update<<<n_blocks, 128, 0, stream>>>(G, st, t_ns, meta, sigma, mu, src_off, src_order, n_src, att,
-                                                  cal, out, rec, scratch, cap, work_counter);
+    k_source_solve<<<n_blocks, 128, 0, stream>>>(st, meta, src_off, src_order, n_src, out, rec, scratch,
+                                                 work_counter);
 }
 
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
