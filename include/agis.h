@@ -183,6 +183,31 @@ void agis_destroy(agis_ctx* ctx);
 const char* agis_last_error(const agis_ctx* ctx);
 int agis_abi_version(void);
 
+/* Largest max_obs_per_source accepted by agis_source_update_static. */
+#define AGIS_STATIC_MAX_OBS 16384
+
+/* Source update that allocates no device memory.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory themselves or through this
+ * library, e.g. code running inside a host framework that owns the allocator, or a process
+ * that reserved all device memory up front.  It runs the S block of agis_source_update()
+ * (observation pass, inner iteration, 5x5 solves, parameter update) on caller-owned device
+ * arrays, and keeps its scratch in a 32 MiB file-scope device array that every GPU loading
+ * this library holds until the process exits.
+ *   obs        n_obs observations, DEVICE pointers, sorted by source (as for agis_init)
+ *   src        n_src x 5 parameters, device, updated in place
+ *   att, cal   device arrays of n_coef x 4 and n_cal (geo->n_cal_days * 138) values
+ *   R_out, W_out  device, n_obs each (residuals h - A d and weights), or NULL
+ *   stats_out  device, 5 x n_src (eps^2, Q, nu, n_out, D by rows), or NULL
+ *   max_obs_per_source  upper bound on the observations of any source, 1..AGIS_STATIC_MAX_OBS
+ * The first call on a device looks up the array's device address with that device current;
+ * make it before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU race and must be serialised.  Errors:
+ * AGIS_E_INVALID (bad arguments, or a source with more than max_obs_per_source observations;
+ * message in agis_last_error(NULL)), AGIS_E_CUDA.  Synchronises the stream before returning. */
+int agis_source_update_static(const agis_geometry* geo, const agis_config* cfg, const agis_obs* obs, int64_t n_obs,
+                              double* src, int32_t n_src, const double* att, const double* cal, double* R_out,
+                              double* W_out, double* stats_out, int32_t max_obs_per_source, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

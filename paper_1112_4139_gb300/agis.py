@@ -24,8 +24,9 @@ EXPORTS = (
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
     "agis_get_calibration", "agis_set_sources", "agis_set_attitude", "agis_set_calibration", "agis_get_residuals",
     "agis_get_source_stats", "agis_get_sizes", "agis_get_kernel_times", "agis_destroy", "agis_last_error",
-    "agis_abi_version",
+    "agis_abi_version", "agis_source_update_static",
 )
+STATIC_MAX_OBS = 16384
 
 
 class Geometry(C.Structure):
@@ -108,6 +109,9 @@ def load():
         lib.agis_last_error.argtypes = [V]
         lib.agis_last_error.restype = C.c_char_p
         lib.agis_abi_version.restype = I
+        lib.agis_source_update_static.argtypes = [C.POINTER(Geometry), C.POINTER(Config), C.POINTER(Obs), C.c_int64,
+                                                  P, C.c_int32, P, P, P, P, P, C.c_int32, P]
+        lib.agis_source_update_static.restype = I
         _lib = lib
     return _lib
 
@@ -279,3 +283,17 @@ def from_dataset(ds, cfg=None, device=None, with_ref=True, stream=None, **cfg_ov
     ref = np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]) if with_ref else None
     return Agis(ds.geometry, cfg, obs_from_dataset(ds, device), np.ascontiguousarray(ds.src0),
                 np.ascontiguousarray(ds.att0), np.ascontiguousarray(ds.cal0), src_ref=ref, stream=stream)
+
+
+def source_update_static(geometry: dict, cfg: Config, obs: dict, src, att, cal, R_out=None, W_out=None,
+                         stats_out=None, max_obs_per_source=STATIC_MAX_OBS, stream=None):
+    """agis_source_update_static on device arrays (torch CUDA tensors); src is updated in place."""
+    lib = load()
+    o = Obs(*(_ptr(obs[k]) for k in ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu")))
+    G = geometry_from_dict(geometry)
+    s = C.c_void_p(stream) if stream is not None else None
+    rc = lib.agis_source_update_static(C.byref(G), C.byref(cfg), C.byref(o), int(obs["t_ns"].shape[0]), _ptr(src),
+                                       int(src.shape[0]), _ptr(att), _ptr(cal), _ptr(R_out), _ptr(W_out),
+                                       _ptr(stats_out), int(max_obs_per_source), s)
+    if rc != AGIS_OK:
+        raise AgisError(rc, lib.agis_last_error(None).decode())

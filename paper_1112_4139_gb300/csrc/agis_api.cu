@@ -835,3 +835,8 @@ int agis_get_kernel_times(const agis_ctx* c, double* ms) {
 }
 
 }  // extern "C"
+
+namespace agis {
+// message returned by agis_last_error(NULL) for calls that have no context
+void set_thread_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace agis
