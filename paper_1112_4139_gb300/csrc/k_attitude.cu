@@ -153,25 +153,55 @@ __global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, c
 // One warp per segment: right-looking robust Cholesky (Algorithm C.1 on the envelope) with
 // forward substitution (C.2) fused, then back substitution (C.3).  Lanes 0..15 hold the
 // 16 columns of the sliding window W[a][b] = N[r+a][r+b] (a <= b); the window moves one row
-// per step by a shuffle, and the column entering at lane 15 is read from the band.
-__global__ void __launch_bounds__(64) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
+// per step by a shuffle, and the column entering at lane 15 comes from a shared-memory
+// double buffer that the warp fills one block of 16 columns ahead (loads in flight while the
+// previous block is factored).
+constexpr int kSolveSegWarps = 2;
+__global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
                                                   const double* __restrict__ bandc, const double* __restrict__ rhs,
                                                   double* __restrict__ urow, double* __restrict__ yv,
                                                   double* __restrict__ x, double tol, int* __restrict__ seg_rd) {
+    __shared__ double colbuf_all[kSolveSegWarps][2][16][17];
     const int lane = threadIdx.x & 31;
-    const int sg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wib = threadIdx.x >> 5;
+    double (*colbuf)[16][17] = colbuf_all[wib];
+    const int sg = blockIdx.x * kSolveSegWarps + wib;
     if (sg >= n_seg) return;
     const int64_t base = seg_row[sg];
     const int64_t n = seg_row[sg + 1] - base;
     const int b = lane;
     const bool act = b < 16;
+    // block kb = columns [16 kb, 16 kb + 16); lane j < 16 loads column 16 kb + j (16 values + rhs)
+    double pre[17];
+    auto load_block = [&](int64_t kb) {
+        const int64_t c = 16 * kb + b;
+        const bool ok = act && c < n;
+#pragma unroll
+        for (int a = 0; a < 16; a++) pre[a] = ok ? bandc[(base + c) * 16 + a] : 0.0;
+        pre[16] = ok ? rhs[base + c] : 0.0;
+    };
+    auto store_block = [&](int64_t kb) {
+        if (act) {
+#pragma unroll
+            for (int a = 0; a < 17; a++) colbuf[kb & 1][b][a] = pre[a];
+        }
+        __syncwarp();
+    };
     double w[16];
 #pragma unroll
     for (int a = 0; a < 16; a++) w[a] = (act && a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
     double dg = (act && b < n) ? bandc[(base + b) * 16] : 0.0;
     double z = (act && b < n) ? rhs[base + b] : 0.0;
+    load_block(1);
+    store_block(1);
+    load_block(2);
     int rd = 0;
     for (int64_t r = 0; r < n; r++) {
+        if (r >= 16 && (r & 15) == 0) {
+            const int64_t m = r >> 4;   // columns of block m+1 are needed from now on
+            store_block(m + 1);
+            load_block(m + 2);
+        }
         const double piv = __shfl_sync(0xffffffffu, w[0], 0);
         const double dg0 = __shfl_sync(0xffffffffu, dg, 0);
         const double urr = piv > tol * dg0 ? sqrt(piv) : 0.0;
@@ -198,10 +228,11 @@ __global__ void __launch_bounds__(64) k_att_solve(int n_seg, const int64_t* __re
         if (b == 15) {
             const int64_t c = r + 16;
             if (c < n) {
+                const double* col = colbuf[(c >> 4) & 1][c & 15];
 #pragma unroll
-                for (int a = 0; a < 16; a++) w[a] = bandc[(base + c) * 16 + (15 - a)];
-                dg = bandc[(base + c) * 16];
-                z = rhs[base + c];
+                for (int a = 0; a < 16; a++) w[a] = col[15 - a];
+                dg = col[0];
+                z = col[16];
             } else {
 #pragma unroll
                 for (int a = 0; a < 16; a++) w[a] = 0.0;
@@ -259,7 +290,8 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
     k_att_assemble<<<blocks, 256, 0, s>>>(n_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
-    k_att_solve<<<(n_seg + 1) / 2, 64, 0, s>>>(n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
+    k_att_solve<<<(n_seg + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
+        n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
     k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att);
 }
 

@@ -301,114 +301,236 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, int64_t n_obs, co
     }
 }
 
-__global__ void __launch_bounds__(128) k_source_solve(
+// General path for one source (any sigma per observation): per-observation passes for every
+// excess-noise step.  Whole warp; the robust sigma vs is given.
+__device__ __noinline__ void solve_general(const Settings& st, int i, int64_t o0, int n, const double* s5, double cosd,
+                                           double* scr, double s2min, double vs, const SrcOutPtrs& out,
+                                           ObsRec* __restrict__ rec, int lane) {
+    if (st.robust) {
+        for (int j = lane; j < n; j += kWarp) {
+            double* e = scr + (size_t)j * kScr;
+            const double x = e[0] / sqrt(e[7]);
+            e[6] = vs > 0.0 ? wfun(x / vs, st.weight_fn) : 1.0;
+        }
+    } else {
+        for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
+    }
+    __syncwarp();
+    double d[5] = {0, 0, 0, 0, 0};
+    double U[15];
+    double y = 0.0, Q = 0.0, Q0 = 0.0;
+    int nu = 0, nout = 0, rd = 0;
+    const int rounds = st.robust ? st.n_rounds + 1 : 1;
+    for (int rnd = 0; rnd < rounds; rnd++) {
+        Sys5 sy;
+        double dprev[5] = {d[0], d[1], d[2], d[3], d[4]};
+        const double yprev = y;
+        y = 0.0;
+        pass_normals(scr, n, lane, 0.0, rnd > 0, dprev, yprev, st.weight_fn, sy, nout);
+        nu = n - nout - 5;
+        rd = chol5(sy.N, U, st.pivot_tol);
+        chol5_solve(U, sy.b, d);
+        double S2;
+        pass_q(scr, n, lane, d, 0.0, Q, S2);
+        Q0 = Q;
+        if (st.robust && nu > 0 && Q0 > (double)nu) {
+            const double tol = 1e-12 * s2min;
+            for (int it = 0; it < st.n_eps; it++) {
+                double dy = (1.0 - Q / (double)nu) * Q / (-S2);
+                y = fmax(0.0, y + dy);
+                pass_normals(scr, n, lane, y, false, dprev, yprev, st.weight_fn, sy, nout);
+                rd = chol5(sy.N, U, st.pivot_tol);
+                chol5_solve(U, sy.b, d);
+                pass_q(scr, n, lane, d, y, Q, S2);
+                if (fabs(dy) <= tol) break;
+            }
+        }
+        __syncwarp();
+    }
+    double chi = 0.0;
+    for (int j = lane; j < n; j += kWarp) {
+        const double* e = scr + (size_t)j * kScr;
+        double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
+        double W = e[6] / (e[7] + y);
+        ObsRec* r = rec + (o0 + j);
+        r->R = R;
+        r->W = W;
+        chi += W * R * R;
+    }
+    chi = warp_sum(chi);
+    if (lane == 0) {
+        double* sp = out.src + 5 * (size_t)i;
+        sp[0] = s5[0] + d[0] / cosd;
+        sp[1] = s5[1] + d[1];
+        sp[2] = s5[2] + d[2];
+        sp[3] = s5[3] + d[3];
+        sp[4] = s5[4] + d[4];
+        for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
+        for (int c = 0; c < 5; c++) {
+            double e[5] = {0, 0, 0, 0, 0};
+            e[c] = 1.0;
+            double x[5];
+            chol5_solve(U, e, x);
+            for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
+        }
+        out.eps2[i] = y;
+        out.q[i] = Q;
+        out.nu[i] = nu;
+        out.nout[i] = nout;
+        out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
+        out.chi2[i] = chi;
+        out.rankdef[i] = rd;
+    }
+    __syncwarp();
+}
+
+// Per-source solve, batched: a warp takes `batch` consecutive sources of the largest-first
+// order.  The warp sweeps each source's observations cooperatively (robust sigma, per-class
+// sums, hand-over records); lane k keeps source k's state and class sums, so the 5x5
+// algebra of the excess-noise steps runs for the whole batch in parallel instead of
+// redundantly in every lane.  Sources whose observations do not have one sigma per class use
+// the general per-observation path.
+constexpr int kSolveWarps = 2;
+__global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
     Settings st, const uint32_t* __restrict__ meta, const int64_t* __restrict__ src_off,
-    const int32_t* __restrict__ src_order, int32_t n_src, SrcOutPtrs out, ObsRec* __restrict__ rec,
+    const int32_t* __restrict__ src_order, int32_t n_src, int batch, SrcOutPtrs out, ObsRec* __restrict__ rec,
     double* __restrict__ scratch, int* work_counter) {
-    __shared__ int hist_all[4 * 256];
-    __shared__ ClassSums cls_all[4];
+    __shared__ int hist_all[kSolveWarps * 256];
+    __shared__ ClassSums sums_all[kSolveWarps][kWarp];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int* hist = hist_all + wib * 256;
+    ClassSums* sums = sums_all[wib];
+    const int rounds = st.robust ? st.n_rounds + 1 : 1;
     for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(work_counter, 1);
-        idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= n_src) break;
-        const int i = src_order[idx];
-        const int64_t o0 = src_off[i];
-        const int n = (int)(src_off[i + 1] - o0);
-        double s5[5];
-#pragma unroll
-        for (int k = 0; k < 5; k++) s5[k] = out.src[5 * (size_t)i + k];
-        if (n == 0) {
-            if (lane == 0) {
-                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = 0.0;
-                for (int k = 0; k < 25; k++) out.cov[25 * (size_t)i + k] = 0.0;
-                out.eps2[i] = out.q[i] = out.dsig[i] = out.chi2[i] = 0.0;
-                out.nu[i] = out.nout[i] = out.rankdef[i] = 0;
-            }
-            continue;
-        }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(work_counter, batch);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_src) break;
+        const int nb = min(batch, n_src - base);
+        // ---- this lane's source
+        const bool mine = lane < nb;
+        const int my_i = mine ? src_order[base + lane] : 0;
+        const int64_t my_o0 = mine ? src_off[my_i] : 0;
+        const int my_n = mine ? (int)(src_off[my_i + 1] - my_o0) : 0;
+        double s5[5] = {0, 0, 0, 0, 0};
+        if (mine)
+            for (int k = 0; k < 5; k++) s5[k] = out.src[5 * (size_t)my_i + k];
         const double cosd = cos(s5[1]);
-        double* scr = scratch + (size_t)o0 * kScr;
-        // ---- per-class sigma ranges of this source
-        double s2min = 1e300;
-        double s2lo[2] = {1e300, 1e300}, s2hi[2] = {-1e300, -1e300};
-        for (int j = lane; j < n; j += kWarp) {
-            const double s2 = scr[(size_t)j * kScr + 7];
-            const int c = meta_kind(meta[o0 + j]);
-            s2lo[c] = fmin(s2lo[c], s2);
-            s2hi[c] = fmax(s2hi[c], s2);
-            s2min = fmin(s2min, s2);
-        }
-        s2min = warp_min(s2min);
-        for (int c = 0; c < 2; c++) {
-            s2lo[c] = warp_min(s2lo[c]);
-            s2hi[c] = -warp_min(-s2hi[c]);
-        }
-        // every AL observation with one sigma and every AC observation with one sigma
-        const bool classes = (s2lo[0] == s2hi[0] || s2lo[0] == 1e300) && (s2lo[1] == s2hi[1] || s2lo[1] == 1e300);
-        __syncwarp();
-        double vs = 0.0;
-        // ---- robust sigma (half the intersextile range of h / sigma)
-        if (st.robust) {
-            const double p1 = 1.0 / 6.0, p5 = 5.0 / 6.0;
-            double h1 = p1 * (double)(n - 1), h5 = p5 * (double)(n - 1);
-            int lo1 = (int)floor(h1), lo5 = (int)floor(h5);
-            double a0, a1, b0, b1;
-            warp_select_pair(scr, n, lo1, hist, lane, a0, a1);
-            warp_select_pair(scr, n, lo5, hist, lane, b0, b1);
-            double q1 = a0 + (h1 - lo1) * (a1 - a0);
-            double q5 = b0 + (h5 - lo5) * (b1 - b0);
-            vs = 0.5 * (q5 - q1);
-            __syncwarp();
-        }
-        if (classes) {
-            // class-sum path: slot 7 holds the class (0 AL, 1 AC)
+        double my_s2c[2] = {1.0, 1.0}, my_s2min = 1.0, my_vs = 0.0;
+        bool my_uniform = false;
+        // ---- per source: sigma per class, robust sigma
+        for (int k = 0; k < nb; k++) {
+            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+            const int n = __shfl_sync(0xffffffffu, my_n, k);
+            if (n == 0) continue;
+            double* scr = scratch + (size_t)o0 * kScr;
+            double s2min = 1e300;
+            double s2lo[2] = {1e300, 1e300}, s2hi[2] = {-1e300, -1e300};
             for (int j = lane; j < n; j += kWarp) {
-                const int64_t o = o0 + j;
-                scr[(size_t)j * kScr + 7] = (double)meta_kind(meta[o]);
+                const double s2 = scr[(size_t)j * kScr + 7];
+                const int c = meta_kind(meta[o0 + j]);
+                s2lo[c] = fmin(s2lo[c], s2);
+                s2hi[c] = fmax(s2hi[c], s2);
+                s2min = fmin(s2min, s2);
+            }
+            s2min = warp_min(s2min);
+            for (int c = 0; c < 2; c++) {
+                s2lo[c] = warp_min(s2lo[c]);
+                s2hi[c] = -warp_min(-s2hi[c]);
+            }
+            const bool uni = (s2lo[0] == s2hi[0] || s2lo[0] == 1e300) && (s2lo[1] == s2hi[1] || s2lo[1] == 1e300);
+            __syncwarp();
+            double vs = 0.0;
+            if (st.robust) {
+                const double p1 = 1.0 / 6.0, p5 = 5.0 / 6.0;
+                const double h1 = p1 * (double)(n - 1), h5 = p5 * (double)(n - 1);
+                const int lo1 = (int)floor(h1), lo5 = (int)floor(h5);
+                double a0, a1, b0, b1;
+                warp_select_pair(scr, n, lo1, hist, lane, a0, a1);
+                warp_select_pair(scr, n, lo5, hist, lane, b0, b1);
+                vs = 0.5 * ((b0 + (h5 - lo5) * (b1 - b0)) - (a0 + (h1 - lo1) * (a1 - a0)));
+                __syncwarp();
+            }
+            if (uni) {
+                for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 7] = (double)meta_kind(meta[o0 + j]);
             }
             __syncwarp();
-            double s2c[2] = {s2lo[0] == 1e300 ? 1.0 : s2lo[0], s2lo[1] == 1e300 ? 1.0 : s2lo[1]};
-            double sigc[2] = {sqrt(s2c[0]), sqrt(s2c[1])};
-            double d[5] = {0, 0, 0, 0, 0};
-            double U[15];
-            double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
-            int nu = 0, nout = 0, rd = 0;
-            const int rounds = st.robust ? st.n_rounds + 1 : 1;
-            ClassSums& cs = cls_all[wib];
-            for (int rnd = 0; rnd < rounds; rnd++) {
-                const double isd[2] = {1.0 / sqrt(s2c[0] + y), 1.0 / sqrt(s2c[1] + y)};
-                const double dprev[5] = {d[0], d[1], d[2], d[3], d[4]};
+            if (lane == k) {
+                my_uniform = uni;
+                my_s2c[0] = s2lo[0] == 1e300 ? 1.0 : s2lo[0];
+                my_s2c[1] = s2lo[1] == 1e300 ? 1.0 : s2lo[1];
+                my_s2min = s2min;
+                my_vs = vs;
+            }
+        }
+        // ---- inner iteration, class-sum path (lane k solves source k)
+        double d[5] = {0, 0, 0, 0, 0};
+        double U[15];
+        for (int q = 0; q < 15; q++) U[q] = 0.0;
+        double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
+        int nu = 0, nout = 0, rd = 0;
+        for (int rnd = 0; rnd < rounds; rnd++) {
+            for (int k = 0; k < nb; k++) {
+                const int n = __shfl_sync(0xffffffffu, my_n, k);
+                const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
+                if (n == 0 || !uni) continue;
+                const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+                double dk[5];
+                for (int a = 0; a < 5; a++) dk[a] = __shfl_sync(0xffffffffu, d[a], k);
+                const double yk = __shfl_sync(0xffffffffu, y, k);
+                const double s2c[2] = {__shfl_sync(0xffffffffu, my_s2c[0], k), __shfl_sync(0xffffffffu, my_s2c[1], k)};
+                const double vsk = __shfl_sync(0xffffffffu, my_vs, k);
+                const double sigc[2] = {sqrt(s2c[0]), sqrt(s2c[1])};
+                const double isd[2] = {1.0 / sqrt(s2c[0] + yk), 1.0 / sqrt(s2c[1] + yk)};
+                double* scr = scratch + (size_t)o0 * kScr;
+                int no = 0;
                 if (!st.robust) {
-                    for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
-                    __syncwarp();
-                    pass_class(scr, n, lane, 2, 0.0, sigc, dprev, isd, st.weight_fn, cs, nout);
+                    if (rnd == 0) {
+                        for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
+                        __syncwarp();
+                    }
+                    pass_class(scr, n, lane, 2, 0.0, sigc, dk, isd, st.weight_fn, sums[k], no);
                 } else {
-                    pass_class(scr, n, lane, rnd == 0 ? 0 : 1, vs, sigc, dprev, isd, st.weight_fn, cs, nout);
+                    pass_class(scr, n, lane, rnd == 0 ? 0 : 1, vsk, sigc, dk, isd, st.weight_fn, sums[k], no);
                 }
-                nu = n - nout - 5;
+                if (lane == k) nout = no;
+            }
+            __syncwarp();
+            if (mine && my_n > 0 && my_uniform) {
+                nu = my_n - nout - 5;
                 y = 0.0;
-                class_solve(cs, s2c, 0.0, st.pivot_tol, U, d, rd, Q, S2);
+                class_solve(sums[lane], my_s2c, 0.0, st.pivot_tol, U, d, rd, Q, S2);
                 Q0 = Q;
                 if (st.robust && nu > 0 && Q0 > (double)nu) {
-                    const double tol = 1e-12 * s2min;
+                    const double tol = 1e-12 * my_s2min;
                     for (int it = 0; it < st.n_eps; it++) {
                         const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
                         y = fmax(0.0, y + dy);
-                        class_solve(cs, s2c, y, st.pivot_tol, U, d, rd, Q, S2);
+                        class_solve(sums[lane], my_s2c, y, st.pivot_tol, U, d, rd, Q, S2);
                         if (fabs(dy) <= tol) break;
                     }
                 }
-                __syncwarp();
             }
-            const double iw[2] = {1.0 / (s2c[0] + y), 1.0 / (s2c[1] + y)};
+            __syncwarp();
+        }
+        // ---- hand-over records and per-source results
+        double my_chi = 0.0;
+        for (int k = 0; k < nb; k++) {
+            const int n = __shfl_sync(0xffffffffu, my_n, k);
+            const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
+            if (n == 0 || !uni) continue;
+            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+            double dk[5];
+            for (int a = 0; a < 5; a++) dk[a] = __shfl_sync(0xffffffffu, d[a], k);
+            const double yk = __shfl_sync(0xffffffffu, y, k);
+            const double iw[2] = {1.0 / (__shfl_sync(0xffffffffu, my_s2c[0], k) + yk),
+                                  1.0 / (__shfl_sync(0xffffffffu, my_s2c[1], k) + yk)};
+            const double* scr = scratch + (size_t)o0 * kScr;
             double chi = 0.0;
             for (int j = lane; j < n; j += kWarp) {
                 const double* e = scr + (size_t)j * kScr;
-                const double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
+                const double R = e[0] - (e[1] * dk[0] + e[2] * dk[1] + e[3] * dk[2] + e[4] * dk[3] + e[5] * dk[4]);
                 const double W = e[6] * iw[e[7] != 0.0 ? 1 : 0];
                 ObsRec* r = rec + (o0 + j);
                 r->R = R;
@@ -416,7 +538,16 @@ __global__ void __launch_bounds__(128) k_source_solve(
                 chi += W * R * R;
             }
             chi = warp_sum(chi);
-            if (lane == 0) {
+            if (lane == k) my_chi = chi;
+        }
+        if (mine && (my_n == 0 || my_uniform)) {
+            const int i = my_i;
+            if (my_n == 0) {
+                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = 0.0;
+                for (int k = 0; k < 25; k++) out.cov[25 * (size_t)i + k] = 0.0;
+                out.eps2[i] = out.q[i] = out.dsig[i] = out.chi2[i] = 0.0;
+                out.nu[i] = out.nout[i] = out.rankdef[i] = 0;
+            } else {
                 double* sp = out.src + 5 * (size_t)i;
                 sp[0] = s5[0] + d[0] / cosd;
                 sp[1] = s5[1] + d[1];
@@ -436,92 +567,25 @@ __global__ void __launch_bounds__(128) k_source_solve(
                 out.nu[i] = nu;
                 out.nout[i] = nout;
                 out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
-                out.chi2[i] = chi;
+                out.chi2[i] = my_chi;
                 out.rankdef[i] = rd;
             }
-            __syncwarp();
-            continue;
-        }
-        // ---- general path: initial downweighting from the robust sigma
-        if (st.robust) {
-            for (int j = lane; j < n; j += kWarp) {
-                double* e = scr + (size_t)j * kScr;
-                double x = e[0] / sqrt(e[7]);
-                e[6] = vs > 0.0 ? wfun(x / vs, st.weight_fn) : 1.0;
-            }
-        } else {
-            for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
         }
         __syncwarp();
-        // ---- inner iteration (Sect. 5.1.2)
-        double d[5] = {0, 0, 0, 0, 0};
-        double U[15];
-        double y = 0.0, Q = 0.0, Q0 = 0.0;
-        int nu = 0, nout = 0, rd = 0;
-        const int rounds = st.robust ? st.n_rounds + 1 : 1;
-        for (int rnd = 0; rnd < rounds; rnd++) {
-            Sys5 sy;
-            double dprev[5] = {d[0], d[1], d[2], d[3], d[4]};
-            const double yprev = y;
-            y = 0.0;
-            pass_normals(scr, n, lane, 0.0, rnd > 0, dprev, yprev, st.weight_fn, sy, nout);
-            nu = n - nout - 5;
-            rd = chol5(sy.N, U, st.pivot_tol);
-            chol5_solve(U, sy.b, d);
-            double S2;
-            pass_q(scr, n, lane, d, 0.0, Q, S2);
-            Q0 = Q;
-            if (st.robust && nu > 0 && Q0 > (double)nu) {
-                const double tol = 1e-12 * s2min;
-                for (int it = 0; it < st.n_eps; it++) {
-                    double dy = (1.0 - Q / (double)nu) * Q / (-S2);
-                    y = fmax(0.0, y + dy);
-                    pass_normals(scr, n, lane, y, false, dprev, yprev, st.weight_fn, sy, nout);
-                    rd = chol5(sy.N, U, st.pivot_tol);
-                    chol5_solve(U, sy.b, d);
-                    pass_q(scr, n, lane, d, y, Q, S2);
-                    if (fabs(dy) <= tol) break;
-                }
-            }
-            __syncwarp();
+        // ---- sources without one sigma per class: general path, one at a time
+        for (int k = 0; k < nb; k++) {
+            const int n = __shfl_sync(0xffffffffu, my_n, k);
+            const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
+            if (n == 0 || uni) continue;
+            const int i = __shfl_sync(0xffffffffu, my_i, k);
+            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+            double sk[5];
+            for (int a = 0; a < 5; a++) sk[a] = __shfl_sync(0xffffffffu, s5[a], k);
+            const double ck = __shfl_sync(0xffffffffu, cosd, k);
+            const double s2m = __shfl_sync(0xffffffffu, my_s2min, k);
+            const double vsk = __shfl_sync(0xffffffffu, my_vs, k);
+            solve_general(st, i, o0, n, sk, ck, scratch + (size_t)o0 * kScr, s2m, vsk, out, rec, lane);
         }
-        // ---- hand-over records: R = h - A d, W = w / (sigma^2 + eps^2)
-        double chi = 0.0;
-        for (int j = lane; j < n; j += kWarp) {
-            const double* e = scr + (size_t)j * kScr;
-            double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
-            double W = e[6] / (e[7] + y);
-            ObsRec* r = rec + (o0 + j);
-            r->R = R;
-            r->W = W;
-            chi += W * R * R;
-        }
-        chi = warp_sum(chi);
-        // ---- per-source results (lane 0); covariance from the last factor (App. C.2)
-        if (lane == 0) {
-            double* sp = out.src + 5 * (size_t)i;
-            sp[0] = s5[0] + d[0] / cosd;
-            sp[1] = s5[1] + d[1];
-            sp[2] = s5[2] + d[2];
-            sp[3] = s5[3] + d[3];
-            sp[4] = s5[4] + d[4];
-            for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
-            for (int c = 0; c < 5; c++) {
-                double e[5] = {0, 0, 0, 0, 0};
-                e[c] = 1.0;
-                double x[5];
-                chol5_solve(U, e, x);
-                for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
-            }
-            out.eps2[i] = y;
-            out.q[i] = Q;
-            out.nu[i] = nu;
-            out.nout[i] = nout;
-            out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
-            out.chi2[i] = chi;
-            out.rankdef[i] = rd;
-        }
-        __syncwarp();
     }
 }
 
@@ -551,8 +615,15 @@ void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_
     if (fb < 1) fb = 1;
     k_obs_forward<<<fb, 256, 0, stream>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
     cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
-    k_source_solve<<<n_blocks, 128, 0, stream>>>(st, meta, src_off, src_order, n_src, out, rec, scratch,
-                                                 work_counter);
+    // batch size: 32 sources per warp when there are enough sources to keep ~16 warps per SM busy
+    int batch = n_src / (152 * 16);
+    batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
+    int warps = (n_src + batch - 1) / batch;
+    int blocks = (warps + kSolveWarps - 1) / kSolveWarps;
+    if (blocks > n_blocks * 4) blocks = n_blocks * 4;
+    if (blocks < 1) blocks = 1;
+    k_source_solve<<<blocks, 32 * kSolveWarps, 0, stream>>>(st, meta, src_off, src_order, n_src, batch, out, rec,
+                                                            scratch, work_counter);
 }
 
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
