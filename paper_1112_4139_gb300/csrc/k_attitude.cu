@@ -10,18 +10,18 @@ __host__ __device__ constexpr int tri16(int i, int j) { return i * 16 - i * (i -
 // 4x4 symmetric upper storage
 __host__ __device__ constexpr int tri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
 
-constexpr int kStage = 18;  // staged per observation: B[4], M[10], r[4]
+constexpr int kStage = 28;  // staged per observation: B[4], M[10], r[4], BB[10]
 
 // One warp per knot interval l (left index), iv = l - 3.  For each observation
 // dR/da = B (x) g and dD/da = -2 B (x) s (Eqs. dfadq, dDldan), so its contribution to the
 // 16x16 block of the interval is W (B B') (x) (g g' + 4 lambda^2 s s') (Eq. normAmod) and
 // to the right-hand side -W B (x) (R g [- 2 lambda^2 D s]).
-__global__ void __launch_bounds__(256) k_att_accum(DevGeo G, double lambda2, int rhs_norm,
+__global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int rhs_norm,
                                                    const uint32_t* __restrict__ perm_t,
                                                    const int64_t* __restrict__ ivl_off, int n_iv,
                                                    const ObsRec* __restrict__ rec, const double* __restrict__ att,
                                                    double* __restrict__ blk) {
-    __shared__ double stage_all[8][kWarp * kStage];
+    __shared__ double stage_all[4][kWarp * kStage];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     double* stg = stage_all[wib];
@@ -74,6 +74,11 @@ __global__ void __launch_bounds__(256) k_att_accum(DevGeo G, double lambda2, int
                     st[14 + c] = W * v;
                     st[c] = B[c];
                 }
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+#pragma unroll
+                    for (int e = c; e < 4; e++) st[18 + tri4(c, e)] = B[c] * B[e];
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < kStage; c++) st[c] = 0.0;
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(256) k_att_accum(DevGeo G, double lambda2, int
                         const int jj = oj[k];
                         const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
                         const int mi = ci <= cj ? tri4(ci, cj) : tri4(cj, ci);
-                        acc[k] += sq[bi] * sq[bj] * sq[4 + mi];
+                        acc[k] += sq[18 + tri4(bi, bj)] * sq[4 + mi];
                     } else {
                         acc[k] -= sq[i >> 2] * sq[14 + (i & 3)];
                     }
@@ -150,81 +155,84 @@ __global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, c
     }
 }
 
-// One warp per segment: right-looking robust Cholesky (Algorithm C.1 on the envelope) with
-// forward substitution (C.2) fused, then back substitution (C.3).  Lanes 0..15 hold the
-// 16 columns of the sliding window W[a][b] = N[r+a][r+b] (a <= b); the window moves one row
-// per step by a shuffle, and the column entering at lane 15 comes from a shared-memory
-// double buffer that the warp fills one block of 16 columns ahead (loads in flight while the
-// previous block is factored).
+// Two segments per warp, one per 16-lane half: right-looking robust Cholesky (Algorithm C.1
+// on the envelope) with forward substitution (C.2) fused, then back substitution (C.3).
+// Lane b of a half holds column b of the sliding window W[a][b] = N[r+a][r+b] (a <= b); the
+// window moves one row per step by a shuffle within the half, and the column entering at
+// lane 15 comes from a shared-memory double buffer filled one block of 16 columns ahead.
+// The pivot's reciprocal is formed once per row and stored in place of U_rr for C.3.
 constexpr int kSolveSegWarps = 2;
 __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
                                                   const double* __restrict__ bandc, const double* __restrict__ rhs,
                                                   double* __restrict__ urow, double* __restrict__ yv,
                                                   double* __restrict__ x, double tol, int* __restrict__ seg_rd) {
-    __shared__ double colbuf_all[kSolveSegWarps][2][16][17];
+    __shared__ double colbuf_all[kSolveSegWarps][2][2][16][17];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double (*colbuf)[16][17] = colbuf_all[wib];
-    const int sg = blockIdx.x * kSolveSegWarps + wib;
-    if (sg >= n_seg) return;
-    const int64_t base = seg_row[sg];
-    const int64_t n = seg_row[sg + 1] - base;
-    const int b = lane;
-    const bool act = b < 16;
-    // block kb = columns [16 kb, 16 kb + 16); lane j < 16 loads column 16 kb + j (16 values + rhs)
+    const int half = lane >> 4;
+    const int b = lane & 15;
+    double (*colbuf)[16][17] = colbuf_all[wib][half];
+    const int sg = (blockIdx.x * kSolveSegWarps + wib) * 2 + half;
+    const bool seg_ok = sg < n_seg;
+    const int64_t base = seg_ok ? seg_row[sg] : 0;
+    const int64_t n = seg_ok ? seg_row[sg + 1] - base : 0;
+    const int64_t n_other = __shfl_xor_sync(0xffffffffu, n, 16);
+    const int64_t n_max = n > n_other ? n : n_other;
+    if (n_max == 0) return;
+    const unsigned FULL = 0xffffffffu;
     double pre[17];
     auto load_block = [&](int64_t kb) {
         const int64_t c = 16 * kb + b;
-        const bool ok = act && c < n;
+        const bool ok = c < n;
 #pragma unroll
         for (int a = 0; a < 16; a++) pre[a] = ok ? bandc[(base + c) * 16 + a] : 0.0;
         pre[16] = ok ? rhs[base + c] : 0.0;
     };
     auto store_block = [&](int64_t kb) {
-        if (act) {
 #pragma unroll
-            for (int a = 0; a < 17; a++) colbuf[kb & 1][b][a] = pre[a];
-        }
+        for (int a = 0; a < 17; a++) colbuf[kb & 1][b][a] = pre[a];
         __syncwarp();
     };
     double w[16];
 #pragma unroll
-    for (int a = 0; a < 16; a++) w[a] = (act && a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
-    double dg = (act && b < n) ? bandc[(base + b) * 16] : 0.0;
-    double z = (act && b < n) ? rhs[base + b] : 0.0;
+    for (int a = 0; a < 16; a++) w[a] = (a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
+    double dg = b < n ? bandc[(base + b) * 16] : 0.0;
+    double z = b < n ? rhs[base + b] : 0.0;
     load_block(1);
     store_block(1);
     load_block(2);
     int rd = 0;
-    for (int64_t r = 0; r < n; r++) {
+    for (int64_t r = 0; r < n_max; r++) {
         if (r >= 16 && (r & 15) == 0) {
-            const int64_t m = r >> 4;   // columns of block m+1 are needed from now on
+            const int64_t m = r >> 4;
             store_block(m + 1);
             load_block(m + 2);
         }
-        const double piv = __shfl_sync(0xffffffffu, w[0], 0);
-        const double dg0 = __shfl_sync(0xffffffffu, dg, 0);
+        const bool live = r < n;
+        const double piv = __shfl_sync(FULL, w[0], 0, 16);
+        const double dg0 = __shfl_sync(FULL, dg, 0, 16);
         const double urr = piv > tol * dg0 ? sqrt(piv) : 0.0;
-        rd += urr == 0.0;
-        double myU = (b == 0) ? urr : (urr > 0.0 ? w[0] / urr : 0.0);
-        if (!act || r + b >= n) myU = (b == 0) ? urr : 0.0;
-        const double zr = __shfl_sync(0xffffffffu, z, 0);
-        const double yr = urr > 0.0 ? zr / urr : 0.0;
-        if (act) urow[(base + r) * 16 + b] = myU;
-        if (b == 0) yv[base + r] = yr;
+        const double inv = urr > 0.0 ? 1.0 / urr : 0.0;
+        if (live) rd += urr == 0.0;
+        double myU = (b == 0) ? urr : w[0] * inv;
+        if (r + b >= n && b > 0) myU = 0.0;
+        const double zr = __shfl_sync(FULL, z, 0, 16);
+        const double yr = zr * inv;
+        if (live) {
+            urow[(base + r) * 16 + b] = (b == 0) ? inv : myU;
+            if (b == 0) yv[base + r] = yr;
+        }
         if (b >= 1) z -= myU * yr;
-        // trailing update W[a][b] -= U[r][r+a] U[r][r+b], 1 <= a <= b
 #pragma unroll
         for (int a = 1; a < 16; a++) {
-            const double ua = __shfl_sync(0xffffffffu, myU, a);
-            if (a <= b && act) w[a] -= ua * myU;
+            const double ua = __shfl_sync(FULL, myU, a, 16);
+            if (a <= b) w[a] -= ua * myU;
         }
-        // move the window: W'[a][b] = W[a+1][b+1]
 #pragma unroll
-        for (int a = 0; a < 15; a++) w[a] = __shfl_down_sync(0xffffffffu, w[a + 1], 1);
+        for (int a = 0; a < 15; a++) w[a] = __shfl_down_sync(FULL, w[a + 1], 1, 16);
         w[15] = 0.0;
-        z = __shfl_down_sync(0xffffffffu, z, 1);
-        dg = __shfl_down_sync(0xffffffffu, dg, 1);
+        z = __shfl_down_sync(FULL, z, 1, 16);
+        dg = __shfl_down_sync(FULL, dg, 1, 16);
         if (b == 15) {
             const int64_t c = r + 16;
             if (c < n) {
@@ -241,19 +249,22 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
             }
         }
     }
-    // back substitution: lane b holds x_{r+b} (b >= 1)
+    // back substitution: lane b of the half holds x_{r+b} (b >= 1); slot 0 of a U row holds 1/U_rr
     double xw = 0.0;
-    for (int64_t r = n - 1; r >= 0; r--) {
-        const double ur = act ? urow[(base + r) * 16 + b] : 0.0;
-        double part = (b >= 1 && act) ? ur * xw : 0.0;
-        part = warp_sum(part);
-        const double urr = __shfl_sync(0xffffffffu, ur, 0);
-        const double xr = urr > 0.0 ? (yv[base + r] - part) / urr : 0.0;
-        if (b == 0) x[base + r] = xr;
-        xw = __shfl_up_sync(0xffffffffu, xw, 1);
+    for (int64_t k = 0; k < n_max; k++) {
+        const int64_t r = n - 1 - k;
+        const bool live = r >= 0;
+        const double ur = live ? urow[(base + r) * 16 + b] : 0.0;
+        double part = (b >= 1) ? ur * xw : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o, 16);
+        const double inv = __shfl_sync(FULL, ur, 0, 16);
+        const double xr = live ? (yv[base + r] - part) * inv : 0.0;
+        if (live && b == 0) x[base + r] = xr;
+        xw = __shfl_up_sync(FULL, xw, 1, 16);
         if (b == 1) xw = xr;
     }
-    if (lane == 0) seg_rd[sg] = rd;
+    if (b == 0 && seg_ok) seg_rd[sg] = rd;
 }
 
 // a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per coefficient.
@@ -276,10 +287,10 @@ __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ s
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
                       int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s) {
     int warps = n_iv;
-    int blocks = (warps + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    int blocks = (warps + 3) / 4;
+    if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
-    k_att_accum<<<blocks, 256, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
+    k_att_accum<<<blocks, 128, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
 }
 
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
@@ -290,7 +301,8 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
     k_att_assemble<<<blocks, 256, 0, s>>>(n_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
-    k_att_solve<<<(n_seg + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
+    const int seg_warps = (n_seg + 1) / 2;
+    k_att_solve<<<(seg_warps + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
         n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
     k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att);
 }
