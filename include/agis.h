@@ -74,8 +74,19 @@ typedef struct agis_config {
     int32_t use_graph;           /* agis_iterate replays one captured CUDA graph per iteration */
     double pivot_tol;            /* robust Cholesky: pivots <= pivot_tol * N_jj count as zero (1e-12) */
     int32_t max_obs_per_source;  /* largest n_i accepted (bounds the S-pass scratch), 0: derived */
-    int32_t reserved[7];
+    int32_t precision;           /* 0: FP64 throughout; 1: mixed (see below)                 */
+    int32_t refresh_every;       /* mixed: full FP64 residual refresh every n source updates */
+    int32_t reserved[5];
 } agis_config;
+
+/* Mixed precision (precision = 1).  The residuals stay FP64; partials and normal-equation
+ * accumulation run in FP32, and the outer block iteration acts as iterative refinement.
+ * Every refresh_every-th source update evaluates the full FP64 observation model
+ * (Eqs. resAL, resAC) and stores R (FP64) with the FP32 partials.  The source updates in
+ * between take the residuals from the linear identity of Eq. precond2:
+ * R <- R + (dR/da) d_a + (dR/dc) d_c after each A and C update, and R <- R - A d after the
+ * source solve.  The 5x5 and banded Cholesky factorisations and the frame rotator stay
+ * FP64. */
 
 /* Observations in structure-of-arrays form, sorted by source index (ascending; any order
  * within a source).  AL and AC components are separate observations (Sect. 3.6). */

@@ -46,7 +46,7 @@ class Config(C.Structure):
         ("lambda_att", C.c_double), ("rhs_norm_term", C.c_int32), ("seg_len", C.c_int32),
         ("seg_overlap", C.c_int32), ("frame_each_iter", C.c_int32), ("block_mask", C.c_int32),
         ("use_graph", C.c_int32), ("pivot_tol", C.c_double), ("max_obs_per_source", C.c_int32),
-        ("reserved", C.c_int32 * 7),
+        ("precision", C.c_int32), ("refresh_every", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 

@@ -24,7 +24,19 @@ void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint3
                       int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s);
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
-                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, cudaStream_t s);
+                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
+                      cudaStream_t s);
+void launch_mix_s(const DevGeo& G, const Settings& st, bool refresh, const int64_t* t_ns, const uint32_t* meta,
+                  const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs, const int64_t* src_off,
+                  const int32_t* src_order, int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out,
+                  MixS* ms, MixT* mt, double* geo, float* d_att, double* d_cal, int n_coef, int n_cal, int* work,
+                  cudaStream_t s);
+void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
+                          const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
+                          double* blk, cudaStream_t s);
+void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
+                    double* dtil, int* rd, double* cal, double* d_cal, cudaStream_t s);
+void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
                 double* dtil, int* rd, double* cal, cudaStream_t s);
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
@@ -173,6 +185,14 @@ struct agis_ctx {
     double* cal = nullptr;
     // S block
     ObsRec* rec = nullptr;
+    // mixed-precision form: records, updates since the last S block, refresh bookkeeping
+    bool mixed = false;
+    MixS* ms = nullptr;
+    MixT* mt = nullptr;
+    float* d_att = nullptr;
+    double* d_cal = nullptr;
+    bool mix_stale = true;   // the records do not describe the current state: evaluate in full
+    int mix_since = 0;       // source updates since the last full evaluation
     double* scratch = nullptr;   // n_obs x 8 doubles, source order
     double* sgeo = nullptr;      // n_src x 16
     int cap = 0, n_sblocks = 0;
@@ -211,8 +231,9 @@ struct agis_ctx {
     bool have_s = false;
     cudaEvent_t ev[12];
     double ktimes[5] = {0, 0, 0, 0, 0};
-    cudaGraphExec_t graph_execs[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per-block graphs: 0 S, 1 A, 2 C, 3 frame, 4 S with a full evaluation (mixed form)
+    cudaGraphExec_t graph_execs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graphs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
@@ -308,23 +329,47 @@ double elapsed(agis_ctx* c, int a, int b) {
 }
 
 // --- the block sequences (enqueue only; no host synchronisation) ---------------------------
-void enqueue_s(agis_ctx* c) {
-    launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
-                         c->src_order, c->n_src, c->att, c->cal, c->so, c->rec, c->sgeo, c->scratch, c->work,
-                         c->n_sblocks, c->stream);
+// mixed form: does the next source update start with a full FP64 evaluation?
+bool s_refresh_due(const agis_ctx* c) {
+    return c->mixed && (c->mix_stale || c->mix_since >= c->cfg.refresh_every);
+}
+void s_done(agis_ctx* c, bool refresh) {
+    if (!c->mixed) return;
+    c->mix_stale = false;
+    c->mix_since = refresh ? 1 : c->mix_since + 1;
+}
+
+void enqueue_s(agis_ctx* c, bool refresh) {
+    if (c->mixed)
+        launch_mix_s(c->G, c->st, refresh, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
+                     c->src_order, c->n_src, c->att, c->cal, c->so, c->ms, c->mt, c->sgeo, c->d_att, c->d_cal,
+                     c->n_coef, c->n_cal, c->work, c->stream);
+    else
+        launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
+                             c->src_order, c->n_src, c->att, c->cal, c->so, c->rec, c->sgeo, c->scratch, c->work,
+                             c->n_sblocks, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
 }
 void enqueue_a(agis_ctx* c) {
-    launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
-                     c->rec, c->att, c->blk, c->stream);
+    if (c->mixed)
+        launch_mix_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, c->ms, c->mt,
+                             c->att, c->blk, c->stream);
+    else
+        launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
+                         c->rec, c->att, c->blk, c->stream);
     launch_att_solve(c->n_seg, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
-                     c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->stream);
+                     c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->mixed ? c->d_att : nullptr,
+                     c->stream);
     launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
 }
 void enqueue_c(agis_ctx* c) {
-    launch_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->rec, c->st.pivot_tol, c->dtil,
-               c->cal_rd, c->cal, c->stream);
+    if (c->mixed)
+        launch_mix_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->ms, c->dtil, c->cal_rd, c->cal, c->d_cal,
+                       c->stream);
+    else
+        launch_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->rec, c->st.pivot_tol, c->dtil,
+                   c->cal_rd, c->cal, c->stream);
     launch_int_sum(c->n_cal, c->cal_rd, c->isum + 1, c->stream);
 }
 void enqueue_frame(agis_ctx* c, const int32_t* subset, int n) {
@@ -368,6 +413,8 @@ void agis_default_config(agis_config* cfg) {
     cfg->use_graph = 1;
     cfg->pivot_tol = 1e-12;
     cfg->max_obs_per_source = 0;
+    cfg->precision = 0;
+    cfg->refresh_every = 8;
 }
 
 static thread_local std::string g_init_err = "no error";
@@ -376,7 +423,7 @@ const char* agis_last_error(const agis_ctx* ctx) { return ctx ? ctx->err.c_str()
 void agis_destroy(agis_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (int b = 0; b < 4; b++) {
+    for (int b = 0; b < 5; b++) {
         if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
         if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
     }
@@ -413,6 +460,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         return bail(fail(c, AGIS_E_INVALID, "null observation array"));
     if (cfg->seg_len < 1 || cfg->seg_overlap < 0 || cfg->n_rounds < 0 || cfg->n_eps < 0)
         return bail(fail(c, AGIS_E_INVALID, "bad segmentation or iteration counts"));
+    if (cfg->precision != 0 && cfg->precision != 1) return bail(fail(c, AGIS_E_INVALID, "precision must be 0 or 1"));
+    if (cfg->precision == 1 && cfg->refresh_every < 1)
+        return bail(fail(c, AGIS_E_INVALID, "refresh_every must be at least 1"));
     for (int i = 0; i < AGIS_N_CCD; i++)
         if (geo->ccd_row[i] < 0 || geo->ccd_row[i] >= AGIS_N_ROW) return bail(fail(c, AGIS_E_INVALID, "bad ccd_row"));
     c->geo = *geo;
@@ -550,8 +600,15 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
             return bail(rc);
     }
     c->n_sblocks = c->n_sm * 8;
-    if ((rc = dalloc(c, &c->rec, n)) ||
-        (rc = dalloc(c, &c->scratch, (size_t)n * kScr)) || (rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
+    c->mixed = cfg->precision == 1;
+    if (c->mixed) {
+        if ((rc = dalloc(c, &c->ms, n)) || (rc = dalloc(c, &c->mt, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
+            (rc = dalloc(c, &c->d_cal, n_cal)))
+            return bail(rc);
+    } else {
+        if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
+    }
+    if ((rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
         (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
         (rc = dalloc(c, &c->so.eps2, n_src)) || (rc = dalloc(c, &c->so.q, n_src)) ||
         (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||
@@ -612,12 +669,14 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
 
 int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     if (!c) return AGIS_E_INVALID;
+    const bool refresh = s_refresh_due(c);
     record(c, 0);
-    enqueue_s(c);
+    enqueue_s(c, refresh);
     record(c, 1);
     AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "stats");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "source update");
     AGIS_CU(c, cudaGetLastError(), "source update kernels");
+    s_done(c, refresh);
     c->have_s = true;
     fill_s_stats(c, c->hstat, out);
     c->ktimes[0] = elapsed(c, 0, 1);
@@ -707,9 +766,11 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     const bool graph = c->cfg.use_graph != 0;
     // one graph per block, so that the blocks can be timed by events between the launches
     if (graph && !c->graphs_ready) {
-        for (int b = 0; b < 4; b++) {
+        for (int b = 0; b < 5; b++) {
+            if (b == 4 && !c->mixed) break;
             AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            if (b == 0) enqueue_s(c);
+            if (b == 0) enqueue_s(c, false);
+            if (b == 4) enqueue_s(c, true);
             if (b == 1) enqueue_a(c);
             if (b == 2) enqueue_c(c);
             if (b == 3 && c->ref) enqueue_frame(c, nullptr, c->n_src);
@@ -720,7 +781,8 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     }
     auto run_block = [&](int b) -> int {
         if (graph) return cuda_check(c, cudaGraphLaunch(c->graph_execs[b], c->stream), "graph launch");
-        if (b == 0) enqueue_s(c);
+        if (b == 0) enqueue_s(c, false);
+        if (b == 4) enqueue_s(c, true);
         if (b == 1) enqueue_a(c);
         if (b == 2) enqueue_c(c);
         if (b == 3) enqueue_frame(c, nullptr, c->n_src);
@@ -728,7 +790,9 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     };
     for (int32_t k = 0; k < n_iter; k++) {
         AGIS_CU(c, cudaEventRecord(c->ev[8], c->stream), "event");
-        if (mask & 1) AGIS_TRY(run_block(0));
+        const bool refresh = (mask & 1) && s_refresh_due(c);
+        if (mask & 1) AGIS_TRY(run_block(refresh ? 4 : 0));
+        if (mask & 1) s_done(c, refresh);
         AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
         if (mask & 2) AGIS_TRY(run_block(1));
         AGIS_CU(c, cudaEventRecord(c->ev[10], c->stream), "event");
@@ -788,6 +852,7 @@ static int set_copy(agis_ctx* c, void* dst, const void* src, size_t bytes) {
     AGIS_CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
     c->have_s = false;
+    c->mix_stale = true;
     return AGIS_OK;
 }
 int agis_set_sources(agis_ctx* c, const double* v) { return c ? set_copy(c, c->src, v, 5 * (size_t)c->n_src * 8) : AGIS_E_INVALID; }
@@ -799,7 +864,10 @@ int agis_get_residuals(agis_ctx* c, double* R_out, double* W_out) {
     if (!c->have_s) return fail(c, AGIS_E_INVALID, "no source update since the last state change");
     if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
     if (!c->tmpW) AGIS_TRY(dalloc(c, &c->tmpW, (size_t)c->n_obs));
-    k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->rec, c->tmpR, c->tmpW);
+    if (c->mixed)
+        launch_mix_rw(c->n_obs, c->ms, c->tmpR, c->tmpW, c->stream);
+    else
+        k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->rec, c->tmpR, c->tmpW);
     if (R_out) AGIS_CU(c, cudaMemcpyAsync(R_out, c->tmpR, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy R");
     if (W_out) AGIS_CU(c, cudaMemcpyAsync(W_out, c->tmpW, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy W");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "residuals");

@@ -46,6 +46,24 @@ struct __align__(16) ObsRec {
 };
 static_assert(sizeof(ObsRec) == 64, "record must be 64 bytes");
 
+// Mixed-precision records (source order), two 32-byte halves.  MixS holds what the source
+// solve reads: the FP64 residual and the FP32 design row (A = (Ap, Aq, Aw, Ap tau, Aq tau),
+// Eq. ubardiff), sigma (negative for AC) and the weight.  MixT holds what the A and C passes
+// gather besides R and W: the attitude partial g, the descriptor and the time.
+struct __align__(16) MixS {
+    double R;       // residual (FP64)
+    float Ap, Aq, Aw, tau;
+    float sig;      // +sigma for AL, -sigma for AC
+    float W;        // w during the source solve, w / (sigma^2 + eps^2) afterwards
+};
+struct __align__(16) MixT {
+    float g[4];     // dR/dq / ||s||
+    uint32_t meta;
+    uint32_t pad;
+    int64_t t_ns;
+};
+static_assert(sizeof(MixS) == 32 && sizeof(MixT) == 32, "mixed records must be 32 bytes");
+
 // Per-source outputs of the S block (device arrays).
 struct SrcOutPtrs {
     double* src;      // n_src x 5, updated in place
@@ -191,6 +209,7 @@ struct ObsOut {
     double R;       // residual
     double A[5];    // -dR/ds'
     double g[4];    // dR/dq / ||s||
+    double tau;     // proper-motion time (years), A[3] = A[0] tau, A[4] = A[1] tau
 };
 
 // Residual and partial derivatives of one observation (FP64).
@@ -267,6 +286,7 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
     double Aq = ((1.0 - ubv) * dot3(ec, S.q) - eub * dot3(vc, S.q)) * sc;
     double Aw = ((1.0 - ubv) * dot3(ec, dpar) - eub * dot3(vc, dpar)) * sc;
     o.A[0] = Ap; o.A[1] = Aq; o.A[2] = Aw; o.A[3] = Ap * tau; o.A[4] = Aq * tau;
+    o.tau = tau;
     // attitude: dR_AL/dq = 2 sec(zeta) q {n,0};  dR_AC/dq = -2 q {m,0}
     double v4[4];
     double gq[4];
@@ -331,6 +351,44 @@ __device__ __forceinline__ void chol5_solve(const double* U, const double* b, do
         for (int k = i + 1; k < 5; k++) s -= U[up5(i, k)] * x[k];
         x[i] = U[up5(i, i)] > 0.0 ? s / U[up5(i, i)] : 0.0;
     }
+}
+
+// ---- per-class sums: when every AL observation of a source has one sigma and every AC
+// observation another, N(y) = sum_c AA_c / (s2_c + y), b(y) = sum_c Ah_c / (s2_c + y) and
+// Q(y) = sum_c [hh_c - 2 d'Ah_c + d'AA_c d] / (s2_c + y): one pass over the observations per
+// weight round serves every excess-noise step (exact algebra; only the rounding differs).
+struct ClassSums {
+    double AA[2][15];
+    double Ah[2][5];
+    double hh[2];
+};
+
+// solve at excess variance y from the class sums; returns Q(y) and S2 = sum num_c/(s2_c+y)^2
+static __device__ __noinline__ void class_solve(const ClassSums& S, const double* s2c, double y, double tol_piv,
+                                            double* U, double* d, int& rd, double& Q, double& S2) {
+    const double i0 = 1.0 / (s2c[0] + y), i1 = 1.0 / (s2c[1] + y);
+    double N[15], b[5];
+#pragma unroll
+    for (int i = 0; i < 15; i++) N[i] = S.AA[0][i] * i0 + S.AA[1][i] * i1;
+#pragma unroll
+    for (int i = 0; i < 5; i++) b[i] = S.Ah[0][i] * i0 + S.Ah[1][i] * i1;
+    rd = chol5(N, U, tol_piv);
+    chol5_solve(U, b, d);
+    double num[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        double dMd = 0.0, db = 0.0;
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+            db += d[a] * S.Ah[c][a];
+            dMd += S.AA[c][up5(a, a)] * d[a] * d[a];
+#pragma unroll
+            for (int k = a + 1; k < 5; k++) dMd += 2.0 * S.AA[c][up5(a, k)] * d[a] * d[k];
+        }
+        num[c] = S.hh[c] - 2.0 * db + dMd;
+    }
+    Q = num[0] * i0 + num[1] * i1;
+    S2 = num[0] * i0 * i0 + num[1] * i1 * i1;
 }
 
 }  // namespace agis

@@ -267,10 +267,11 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
     if (b == 0 && seg_ok) seg_rd[sg] = rd;
 }
 
-// a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per coefficient.
+// a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per
+// coefficient.  The mixed form also accumulates the update in d_att (FP32).
 __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ seg_u, const int32_t* __restrict__ seg_n,
                             const int64_t* __restrict__ seg_row, const double* __restrict__ x,
-                            double* __restrict__ att) {
+                            double* __restrict__ att, float* __restrict__ d_att) {
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < n_coef; n += gridDim.x * blockDim.x) {
         int lo = 0, hi = n_seg - 1;
         while (lo < hi) {
@@ -280,7 +281,10 @@ __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ s
         const int sg = lo;
         const int64_t r0 = seg_row[sg] + 4 * (int64_t)(n - seg_n[2 * sg]);
 #pragma unroll
-        for (int c = 0; c < 4; c++) att[4 * (int64_t)n + c] += x[r0 + c];
+        for (int c = 0; c < 4; c++) {
+            att[4 * (int64_t)n + c] += x[r0 + c];
+            if (d_att) d_att[4 * (int64_t)n + c] += (float)x[r0 + c];
+        }
     }
 }
 
@@ -293,9 +297,11 @@ void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint3
     k_att_accum<<<blocks, 128, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
 }
 
+// d_att (mixed form only, else null) accumulates the applied update in FP32
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
-                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, cudaStream_t s) {
+                      double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
+                      cudaStream_t s) {
     int64_t total = n_rows * 16;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
@@ -304,7 +310,7 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
     const int seg_warps = (n_seg + 1) / 2;
     k_att_solve<<<(seg_warps + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
         n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
-    k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att);
+    k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att, d_att);
 }
 
 }  // namespace agis

@@ -152,16 +152,6 @@ __device__ __forceinline__ void pass_q(const double* scr, int n, int lane, const
     S2 = warp_sum(s);
 }
 
-// ---- per-class sums: when every AL observation of a source has one sigma and every AC
-// observation another, N(y) = sum_c AA_c / (s2_c + y), b(y) = sum_c Ah_c / (s2_c + y) and
-// Q(y) = sum_c [hh_c - 2 d'Ah_c + d'AA_c d] / (s2_c + y): one pass over the observations per
-// weight round serves every excess-noise step (exact algebra; only the rounding differs).
-struct ClassSums {
-    double AA[2][15];
-    double Ah[2][5];
-    double hh[2];
-};
-
 // Sums of one class.  mode 0: w = wfun(x / vs) with x = h / sigma (initial downweighting);
 // mode 1: refresh w = wfun(R / sqrt(s2 + y_prev)) with R = h - A d_prev; mode 2: keep the stored
 // w.  The new w is stored in the scratch.  Each observation belongs to exactly one class, so
@@ -227,34 +217,6 @@ __device__ __forceinline__ void pass_class(double* scr, int n, int lane, int mod
     }
     __syncwarp();
     nout = nc[0] + nc[1];
-}
-
-// solve at excess variance y from the class sums; returns Q(y) and S2 = sum num_c/(s2_c+y)^2
-__device__ __noinline__ void class_solve(const ClassSums& S, const double* s2c, double y, double tol_piv,
-                                            double* U, double* d, int& rd, double& Q, double& S2) {
-    const double i0 = 1.0 / (s2c[0] + y), i1 = 1.0 / (s2c[1] + y);
-    double N[15], b[5];
-#pragma unroll
-    for (int i = 0; i < 15; i++) N[i] = S.AA[0][i] * i0 + S.AA[1][i] * i1;
-#pragma unroll
-    for (int i = 0; i < 5; i++) b[i] = S.Ah[0][i] * i0 + S.Ah[1][i] * i1;
-    rd = chol5(N, U, tol_piv);
-    chol5_solve(U, b, d);
-    double num[2];
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        double dMd = 0.0, db = 0.0;
-#pragma unroll
-        for (int a = 0; a < 5; a++) {
-            db += d[a] * S.Ah[c][a];
-            dMd += S.AA[c][up5(a, a)] * d[a] * d[a];
-#pragma unroll
-            for (int k = a + 1; k < 5; k++) dMd += 2.0 * S.AA[c][up5(a, k)] * d[a] * d[k];
-        }
-        num[c] = S.hh[c] - 2.0 * db + dMd;
-    }
-    Q = num[0] * i0 + num[1] * i1;
-    S2 = num[0] * i0 * i0 + num[1] * i1 * i1;
 }
 
 // Per-source geometry for the observation pass: p, q, r (Eq. normal-triad), parameters, cos(delta).
@@ -624,6 +586,10 @@ void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_
     if (blocks < 1) blocks = 1;
     k_source_solve<<<blocks, 32 * kSolveWarps, 0, stream>>>(st, meta, src_off, src_order, n_src, batch, out, rec,
                                                             scratch, work_counter);
+}
+
+void launch_src_geo(int32_t n_src, const double* src, double* geo, cudaStream_t s) {
+    k_src_geo<<<(n_src + 255) / 256 > 0 ? (n_src + 255) / 256 : 1, 256, 0, s>>>(n_src, src, geo);
 }
 
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
