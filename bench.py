@@ -2,10 +2,12 @@
 
 One step = one S[ACG] iteration (S pass and 5x5 solves, A pass and segmented banded
 Cholesky, C pass and constraint projection, frame rotator) over the whole synthetic
-workload, replayed as one CUDA graph.  Inputs are resident in HBM for `value`; `e2e`
+workload, replayed as per-block CUDA graphs.  Inputs are resident in HBM for `value`; `e2e`
 repeats the measurement through the C ABI from host buffers (upload, set-up, one
-iteration, read-back of the updated sources).  `--impl reference` times the FP64 oracle
-on the host cores on a bounded sample of the same workload.
+iteration, read-back of the updated sources).  The headline form is FP64 (`--precision
+mixed` makes the mixed-precision form the headline); the other form is timed on the same
+data and reported beside it, the mixed form over whole refresh cycles.  `--impl reference`
+times the FP64 oracle on the host cores on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 For N > 1 (launched with torch.distributed.run) every rank runs an independent replica:
@@ -28,11 +30,18 @@ WORKLOADS = {
     "scale5yr": "1M sources, 5 yr, 30-s knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
     "small1yr": "10k sources, 1 yr, 1-h knots, 1-day calibration, sigma_AL 100 uas, 1% outliers",
 }
-# kernels launched by one iteration: S (source geometry, observation pass, per-source solve,
-# stats), A (accumulate, assemble,
-# solve, apply, rank-defect sum), C (accumulate, project, rank-defect sum), frame (normals,
-# solve, apply sources, apply attitude)
-KERNELS_PER_STEP = 16
+# kernels launched by one iteration, (with a full FP64 evaluation, with the linearized pass):
+# FP64 form: S (source geometry, observation pass, per-source solve, stats), A (accumulate,
+# assemble, solve, apply, rank-defect sum), C (accumulate, project, rank-defect sum), frame
+# (normals, solve, apply sources, apply attitude) = 16.  Mixed form: the S pass is source
+# geometry + full evaluation, or the one linearized-correction kernel; the S solves are
+# scale/round-0 sums, 5 rounds of 5x5 algebra, 4 rounds of sums, final pass, per-observation
+# path, stats = 13 (default 4 reweighting rounds); A, C and frame as above.
+KERNELS_PER_STEP = {"fp64": (16, 16), "mixed": (2 + 13 + 12, 1 + 13 + 12)}
+FP64_PEAK_TFLOPS = 1.25
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes per observation of the linearized observation pass (see time_form)
+MIX_PASS_BYTES = 8 + 16 + 4 + 8 + 8
 
 
 def parse():
@@ -45,6 +54,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--n-src", type=int, default=0, help="override the number of sources (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="form timed for the headline value (the other is reported beside it)")
+    ap.add_argument("--refresh-every", type=int, default=8, help="mixed form: full FP64 evaluation period")
+    ap.add_argument("--single-form", action="store_true", help="time only the --precision form")
+    ap.add_argument("--knot-dt-s", type=int, default=0, help="override the attitude knot interval (testing)")
     return ap.parse_args()
 
 
@@ -176,6 +190,8 @@ def make_dataset(args):
     over = {}
     if args.n_src:
         over["n_src"] = args.n_src
+    if args.knot_dt_s:
+        over["knot_dt_s"] = args.knot_dt_s
     t = time.perf_counter()
     ds = synth.simulate(synth.config(args.workload, **over))
     return ds, time.perf_counter() - t
@@ -202,6 +218,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_form(agis, ds, stream, cfg, steps, warmup, local, dist):
+    """Device-resident timing of `steps` iterations after `warmup` untimed ones."""
+    import torch
+    obs_d = agis.obs_from_dataset(ds, device="cuda")
+    t = time.perf_counter()
+    g = agis.Agis(ds.geometry, cfg, obs_d, np.ascontiguousarray(ds.src0), np.ascontiguousarray(ds.att0),
+                  np.ascontiguousarray(ds.cal0), src_ref=np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]),
+                  stream=stream.cuda_stream)
+    t_init = time.perf_counter() - t
+    del obs_d
+    g.iterate(warmup)
+    # flush-free timing: the inputs (>= tens of GB) are far larger than the 129 MB L2
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    its = g.iterate(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    g.close()
+    full = [it for it in its if it["s"]["full_eval"]]
+    lin = [it for it in its if not it["s"]["full_eval"]]
+    med = lambda xs: float(np.median(xs)) if xs else None
+    return {"ms": ms, "t_init": t_init, "clocks": clocks, "n_full_eval": len(full),
+            "s_ms": med([it["s"]["elapsed_ms"] for it in its]), "a_ms": med([it["a"]["elapsed_ms"] for it in its]),
+            "c_ms": med([it["c"]["elapsed_ms"] for it in its]),
+            "pass_full_ms": med([it["s"]["pass_ms"] for it in full]),
+            "pass_lin_ms": med([it["s"]["pass_ms"] for it in lin]),
+            "solve_ms": med([it["s"]["elapsed_ms"] - it["s"]["pass_ms"] for it in its])}
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -220,40 +278,20 @@ def main():
     from paper_1112_4139_gb300 import agis
     ds, t_gen = make_dataset(args)
     stream = torch.cuda.Stream()
-    cfg = agis.default_config(seg_len=2880 if ds.geometry["knot_dt_ns"] == 30_000_000_000 else 720,
-                              use_graph=1, frame_each_iter=1)
-    # ---- device-resident inputs
-    obs_d = agis.obs_from_dataset(ds, device="cuda")
-    t = time.perf_counter()
-    g = agis.Agis(ds.geometry, cfg, obs_d, np.ascontiguousarray(ds.src0), np.ascontiguousarray(ds.att0),
-                  np.ascontiguousarray(ds.cal0), src_ref=np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]),
-                  stream=stream.cuda_stream)
-    t_init = time.perf_counter() - t
-    del obs_d
-    g.iterate(args.warmup)
-    # flush-free timing: the inputs (>= tens of GB) are far larger than the 129 MB L2
-    sampler = ClockSampler(local)
-    sampler.start()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    its = g.iterate(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * ds.n_obs / (ms * 1e-3)
-    s_ms = float(np.median([it["s"]["elapsed_ms"] for it in its]))
-    a_ms = float(np.median([it["a"]["elapsed_ms"] for it in its]))
-    g.close()
+    seg_len = 2880 if ds.geometry["knot_dt_ns"] <= 30_000_000_000 else 720
+    forms = {"fp64": dict(precision=0), "mixed": dict(precision=1, refresh_every=args.refresh_every)}
+    head = args.precision
+    other = "mixed" if head == "fp64" else "fp64"
+    cfgs = {k: agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, **v) for k, v in forms.items()}
+    # the mixed form is timed over whole refresh cycles, so its per-iteration time includes
+    # the full FP64 evaluation at its share
+    cyc = max(1, args.refresh_every)
+    steps_of = {"fp64": args.steps, "mixed": cyc * max(1, -(-args.steps // cyc))}
+    res = {head: time_form(agis, ds, stream, cfgs[head], steps_of[head], args.warmup, local, dist)}
+    if not args.single_form:
+        res[other] = time_form(agis, ds, stream, cfgs[other], steps_of[other], args.warmup, local, dist)
+    r = res[head]
+    value = world * ds.n_obs / (r["ms"] * 1e-3)
     # ---- end to end through the C ABI from pinned host buffers
     import torch as T
     host = {k: T.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in agis.obs_from_dataset(ds).items()}
@@ -269,7 +307,7 @@ def main():
     for k in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        ge = agis.Agis(ds.geometry, cfg, host, src0, att0, cal0, src_ref=ref, stream=stream.cuda_stream)
+        ge = agis.Agis(ds.geometry, cfgs[head], host, src0, att0, cal0, src_ref=ref, stream=stream.cuda_stream)
         ge.iterate(1)
         ge.sources(out=out_src.numpy())
         torch.cuda.synchronize()
@@ -277,31 +315,59 @@ def main():
         ge.close()
     e2e = world * ds.n_obs / float(np.median(e2e_times)) if e2e_times else None
     peaks = load_peaks()
-    # FP64 arithmetic bound: the S pass is limited by the FP64 pipe (the design doc derives the
-    # peak from the FP64 unit count and clock: 1.25 TFLOP/s nominal for GB300)
-    fp64_peak = 1.25
-    achieved = S_FLOPS_PER_OBS * ds.n_obs / (s_ms * 1e-3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+
+    def fp64_roofline(x):
+        # FP64 arithmetic bound of the S block (FP64 pass + FP64 per-source solves); the peak
+        # is the FP64 unit count x clock (nominal 1.25 TFLOP/s on GB300)
+        achieved = S_FLOPS_PER_OBS * ds.n_obs / (x["s_ms"] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_obs_forward + k_source_solve (S block, FP64)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock)", "flops_per_obs": S_FLOPS_PER_OBS}
+
+    def mixed_roofline(x):
+        # HBM bound of the linearized observation pass (k_mix_correct): algorithmic bytes per
+        # observation = t (8) + g (16) + calibration index (4) + R read (8) + R written (8)
+        if not x["pass_lin_ms"]:
+            return None
+        achieved = MIX_PASS_BYTES * ds.n_obs / (x["pass_lin_ms"] * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "k_mix_correct (linearized observation pass)", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": hbm_src, "bytes_per_obs": MIX_PASS_BYTES}
+
+    def summary(name, x):
+        d = {"ms_per_step": x["ms"], "value": world * ds.n_obs / (x["ms"] * 1e-3), "unit": "obs/s",
+             "block_ms": {"S": x["s_ms"], "S_pass_full": x["pass_full_ms"], "S_pass_linearized": x["pass_lin_ms"],
+                          "S_solve": x["solve_ms"], "A": x["a_ms"], "C": x["c_ms"],
+                          "rest": x["ms"] - x["s_ms"] - x["a_ms"] - x["c_ms"]},
+             "t_init_s": round(x["t_init"], 2), "clocks": x["clocks"]}
+        if name == "mixed":
+            d.update({"dtype": "f32+f64", "refresh_every": args.refresh_every, "full_evals_timed": x["n_full_eval"],
+                      "roofline": mixed_roofline(x)})
+        else:
+            d.update({"dtype": "f64", "roofline": fp64_roofline(x)})
+        return d
+
     line = {
         "metric": "AL+AC observations/s per AGIS iteration", "value": value, "unit": "obs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": steps_of[head], "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs,
-                   "n_src": ds.n_src, "n_coef": ds.n_coef, "n_cal": ds.n_cal,
+                   "n_src": ds.n_src, "n_coef": ds.n_coef, "n_cal": ds.n_cal, "precision": head,
                    "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "t_generate_s": round(t_gen, 1), "t_init_s": round(t_init, 2)},
+                   "t_generate_s": round(t_gen, 1), "t_init_s": round(r["t_init"], 2)},
         "e2e": ({"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
                 if e2e is not None else None),
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
-        "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": "k_obs_forward + k_source_solve (S pass, FP64)", "achieved": achieved,
-                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                     "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock), not in MEASURED_PEAKS.json",
-                     "flops_per_obs": S_FLOPS_PER_OBS},
-        "block_ms": {"S": s_ms, "A": a_ms, "rest": ms - s_ms - a_ms},
+        "gpu_launches": (KERNELS_PER_STEP[head][0] * r["n_full_eval"] +
+                         KERNELS_PER_STEP[head][1] * (steps_of[head] - r["n_full_eval"])),
+        "clocks": r["clocks"],
+        "roofline": fp64_roofline(r) if head == "fp64" else mixed_roofline(r),
+        "block_ms": summary(head, r)["block_ms"],
     }
-    if peaks.get("hbm_gbs"):
-        line["roofline"]["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    if other in res:
+        line[other] = summary(other, res[other])
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ds)
     if rank == 0:

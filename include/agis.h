@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 1
+#define AGIS_ABI_VERSION 2
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -86,7 +86,10 @@ typedef struct agis_config {
  * between take the residuals from the linear identity of Eq. precond2:
  * R <- R + (dR/da) d_a + (dR/dc) d_c after each A and C update, and R <- R - A d after the
  * source solve.  The 5x5 and banded Cholesky factorisations and the frame rotator stay
- * FP64. */
+ * FP64.  The first source update after agis_init or an agis_set_* call always refreshes.
+ * Device memory per observation: 64 bytes of records (128 in the FP64 form) besides the
+ * inputs.  Converged solutions agree with the FP64 form to well below 1 uas; between
+ * refreshes the residuals carry second-order terms of the updates since the last refresh. */
 
 /* Observations in structure-of-arrays form, sorted by source index (ascending; any order
  * within a source).  AL and AC components are separate observations (Sect. 3.6). */
@@ -109,6 +112,9 @@ typedef struct agis_block_stats {
     int64_t rank_defect;         /* robust Cholesky rank-defect count (App. C)           */
     double d_rms[5];             /* S: RMS of the 5 parameter updates                    */
     double elapsed_ms;           /* device time of the block (CUDA events)               */
+    double pass_ms;              /* S: device time of the observation pass within it     */
+    int32_t full_eval;           /* S: 1 if the pass evaluated the full FP64 model       */
+    int32_t reserved_;
 } agis_block_stats;
 
 typedef struct agis_iter_stats {

@@ -19,6 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
+ABI_VERSION = 2  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -57,11 +58,13 @@ class Obs(C.Structure):
 
 class BlockStats(C.Structure):
     _fields_ = [("chi2", C.c_double), ("q_sum", C.c_double), ("nu_sum", C.c_int64), ("n_out", C.c_int64),
-                ("rank_defect", C.c_int64), ("d_rms", C.c_double * 5), ("elapsed_ms", C.c_double)]
+                ("rank_defect", C.c_int64), ("d_rms", C.c_double * 5), ("elapsed_ms", C.c_double),
+                ("pass_ms", C.c_double), ("full_eval", C.c_int32), ("reserved_", C.c_int32)]
 
     def as_dict(self):
         return dict(chi2=self.chi2, q_sum=self.q_sum, nu_sum=self.nu_sum, n_out=self.n_out,
-                    rank_defect=self.rank_defect, d_rms=list(self.d_rms), elapsed_ms=self.elapsed_ms)
+                    rank_defect=self.rank_defect, d_rms=list(self.d_rms), elapsed_ms=self.elapsed_ms,
+                    pass_ms=self.pass_ms, full_eval=self.full_eval)
 
 
 class IterStats(C.Structure):
@@ -112,6 +115,8 @@ def load():
         lib.agis_source_update_static.argtypes = [C.POINTER(Geometry), C.POINTER(Config), C.POINTER(Obs), C.c_int64,
                                                   P, C.c_int32, P, P, P, P, P, C.c_int32, P]
         lib.agis_source_update_static.restype = I
+        if lib.agis_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"libagis.so has ABI {lib.agis_abi_version()}, this binding {ABI_VERSION}: rebuild")
         _lib = lib
     return _lib
 

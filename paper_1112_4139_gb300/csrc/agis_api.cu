@@ -12,11 +12,13 @@
 #include "agis_internal.cuh"
 
 namespace agis {
-void launch_source_update(const DevGeo& G, const Settings& st, const int64_t* t_ns, const uint32_t* meta,
-                          const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs,
-                          const int64_t* src_off, const int32_t* src_order, int32_t n_src, const double* att,
-                          const double* cal, const SrcOutPtrs& out, ObsRec* rec, double* geo, double* scratch,
-                          int* work_counter, int n_blocks, cudaStream_t stream);
+void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+                     const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
+                     const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
+                     cudaStream_t stream);
+void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_order,
+                         int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch, int* work_counter,
+                         int n_blocks, cudaStream_t stream);
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
@@ -26,16 +28,17 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
                       cudaStream_t s);
-void launch_mix_s(const DevGeo& G, const Settings& st, bool refresh, const int64_t* t_ns, const uint32_t* meta,
-                  const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs, const int64_t* src_off,
-                  const int32_t* src_order, int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out,
-                  MixS* ms, MixT* mt, double* geo, float* d_att, double* d_cal, int n_coef, int n_cal, int* work,
-                  cudaStream_t s);
+void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+                     const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
+                     const double* att, const double* cal, MixS* ms, MixT* mt, double* geo, float* d_att,
+                     float2* d_cal, int n_coef, int n_cal, cudaStream_t s);
+void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_order, int32_t n_src,
+                      const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s);
 void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
                           const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
                           double* blk, cudaStream_t s);
 void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
-                    double* dtil, int* rd, double* cal, double* d_cal, cudaStream_t s);
+                    double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s);
 void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
                 double* dtil, int* rd, double* cal, cudaStream_t s);
@@ -190,7 +193,8 @@ struct agis_ctx {
     MixS* ms = nullptr;
     MixT* mt = nullptr;
     float* d_att = nullptr;
-    double* d_cal = nullptr;
+    float2* d_cal = nullptr;
+    MixSrcWork mw{};
     bool mix_stale = true;   // the records do not describe the current state: evaluate in full
     int mix_since = 0;       // source updates since the last full evaluation
     double* scratch = nullptr;   // n_obs x 8 doubles, source order
@@ -229,11 +233,14 @@ struct agis_ctx {
     double* hstat = nullptr;      // 10 S + 6 frame
     long long* hisum = nullptr;   // 2
     bool have_s = false;
-    cudaEvent_t ev[12];
+    static constexpr int kEvents = 14;
+    cudaEvent_t ev[kEvents];
     double ktimes[5] = {0, 0, 0, 0, 0};
-    // per-block graphs: 0 S, 1 A, 2 C, 3 frame, 4 S with a full evaluation (mixed form)
-    cudaGraphExec_t graph_execs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graphs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // per-block graphs: 0 S observation pass (FP64 model, or the mixed form's linearized
+    // correction), 1 A, 2 C, 3 frame, 4 mixed S pass with the full FP64 model, 5 S solves
+    static constexpr int kGraphs = 6;
+    cudaGraphExec_t graph_execs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graphs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
@@ -339,15 +346,21 @@ void s_done(agis_ctx* c, bool refresh) {
     c->mix_since = refresh ? 1 : c->mix_since + 1;
 }
 
-void enqueue_s(agis_ctx* c, bool refresh) {
+// S block in two parts: the observation pass (timed separately) and the per-source solves
+void enqueue_s_pass(agis_ctx* c, bool refresh) {
     if (c->mixed)
-        launch_mix_s(c->G, c->st, refresh, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
-                     c->src_order, c->n_src, c->att, c->cal, c->so, c->ms, c->mt, c->sgeo, c->d_att, c->d_cal,
-                     c->n_coef, c->n_cal, c->work, c->stream);
+        launch_mix_pass(c->G, refresh, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src,
+                        c->att, c->cal, c->ms, c->mt, c->sgeo, c->d_att, c->d_cal, c->n_coef, c->n_cal, c->stream);
     else
-        launch_source_update(c->G, c->st, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->src_off,
-                             c->src_order, c->n_src, c->att, c->cal, c->so, c->rec, c->sgeo, c->scratch, c->work,
-                             c->n_sblocks, c->stream);
+        launch_obs_pass(c->G, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
+                        c->cal, c->rec, c->sgeo, c->scratch, c->stream);
+}
+void enqueue_s_solve(agis_ctx* c) {
+    if (c->mixed)
+        launch_mix_solve(c->st, c->src_off, c->src_order, c->n_src, c->so, c->ms, c->mw, c->stream);
+    else
+        launch_source_solve(c->st, c->meta, c->src_off, c->src_order, c->n_src, c->so, c->rec, c->scratch, c->work,
+                            c->n_sblocks, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
 }
@@ -423,7 +436,7 @@ const char* agis_last_error(const agis_ctx* ctx) { return ctx ? ctx->err.c_str()
 void agis_destroy(agis_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (int b = 0; b < 5; b++) {
+    for (int b = 0; b < agis_ctx::kGraphs; b++) {
         if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
         if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
     }
@@ -431,7 +444,7 @@ void agis_destroy(agis_ctx* c) {
     if (c->hstat) cudaFreeHost(c->hstat);
     if (c->hisum) cudaFreeHost(c->hisum);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-    for (int i = 0; i < 12; i++)
+    for (int i = 0; i < agis_ctx::kEvents; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;
 }
@@ -442,7 +455,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     if (!out) return AGIS_E_INVALID;
     *out = nullptr;
     agis_ctx* c = new agis_ctx();
-    for (int i = 0; i < 12; i++) c->ev[i] = nullptr;
+    for (int i = 0; i < agis_ctx::kEvents; i++) c->ev[i] = nullptr;
     auto bail = [&](int code) {
         g_init_err = c->err;
         agis_destroy(c);
@@ -513,7 +526,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     st.lambda2 = cfg->lambda_att * cfg->lambda_att;
     st.rhs_norm_term = cfg->rhs_norm_term;
     st.pivot_tol = cfg->pivot_tol;
-    for (int i = 0; i < 12; i++) cudaEventCreate(&c->ev[i]);
+    for (int i = 0; i < agis_ctx::kEvents; i++) cudaEventCreate(&c->ev[i]);
     if (cudaMallocHost(&c->hstat, 32 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->hisum, 4 * sizeof(long long)) != cudaSuccess)
         return bail(fail(c, AGIS_E_OOM, "pinned host buffer"));
@@ -603,7 +616,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     c->mixed = cfg->precision == 1;
     if (c->mixed) {
         if ((rc = dalloc(c, &c->ms, n)) || (rc = dalloc(c, &c->mt, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
-            (rc = dalloc(c, &c->d_cal, n_cal)))
+            (rc = dalloc(c, &c->d_cal, n_cal)) || (rc = dalloc(c, &c->mw.scale, n_src)) ||
+            (rc = dalloc(c, &c->mw.round, n_src)) || (rc = dalloc(c, &c->mw.fin, n_src)) ||
+            (rc = dalloc(c, &c->mw.sums, n_src)))
             return bail(rc);
     } else {
         if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
@@ -671,7 +686,9 @@ int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     if (!c) return AGIS_E_INVALID;
     const bool refresh = s_refresh_due(c);
     record(c, 0);
-    enqueue_s(c, refresh);
+    enqueue_s_pass(c, refresh);
+    record(c, 13);
+    enqueue_s_solve(c);
     record(c, 1);
     AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "stats");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "source update");
@@ -680,7 +697,11 @@ int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     c->have_s = true;
     fill_s_stats(c, c->hstat, out);
     c->ktimes[0] = elapsed(c, 0, 1);
-    if (out) out->elapsed_ms = c->ktimes[0];
+    if (out) {
+        out->elapsed_ms = c->ktimes[0];
+        out->pass_ms = elapsed(c, 0, 13);
+        out->full_eval = (!c->mixed || refresh) ? 1 : 0;
+    }
     if (!std::isfinite(c->hstat[0])) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2 after the source update");
     return AGIS_OK;
 }
@@ -766,11 +787,12 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     const bool graph = c->cfg.use_graph != 0;
     // one graph per block, so that the blocks can be timed by events between the launches
     if (graph && !c->graphs_ready) {
-        for (int b = 0; b < 5; b++) {
-            if (b == 4 && !c->mixed) break;
+        for (int b = 0; b < agis_ctx::kGraphs; b++) {
+            if (b == 4 && !c->mixed) continue;
             AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            if (b == 0) enqueue_s(c, false);
-            if (b == 4) enqueue_s(c, true);
+            if (b == 0) enqueue_s_pass(c, false);
+            if (b == 4) enqueue_s_pass(c, true);
+            if (b == 5) enqueue_s_solve(c);
             if (b == 1) enqueue_a(c);
             if (b == 2) enqueue_c(c);
             if (b == 3 && c->ref) enqueue_frame(c, nullptr, c->n_src);
@@ -781,8 +803,9 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     }
     auto run_block = [&](int b) -> int {
         if (graph) return cuda_check(c, cudaGraphLaunch(c->graph_execs[b], c->stream), "graph launch");
-        if (b == 0) enqueue_s(c, false);
-        if (b == 4) enqueue_s(c, true);
+        if (b == 0) enqueue_s_pass(c, false);
+        if (b == 4) enqueue_s_pass(c, true);
+        if (b == 5) enqueue_s_solve(c);
         if (b == 1) enqueue_a(c);
         if (b == 2) enqueue_c(c);
         if (b == 3) enqueue_frame(c, nullptr, c->n_src);
@@ -792,6 +815,8 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
         AGIS_CU(c, cudaEventRecord(c->ev[8], c->stream), "event");
         const bool refresh = (mask & 1) && s_refresh_due(c);
         if (mask & 1) AGIS_TRY(run_block(refresh ? 4 : 0));
+        AGIS_CU(c, cudaEventRecord(c->ev[12], c->stream), "event");
+        if (mask & 1) AGIS_TRY(run_block(5));
         if (mask & 1) s_done(c, refresh);
         AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
         if (mask & 2) AGIS_TRY(run_block(1));
@@ -817,6 +842,8 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             if (do_frame)
                 for (int i = 0; i < 6; i++) it.frame[i] = c->hstat[16 + i];
             it.s.elapsed_ms = elapsed(c, 8, 9);
+            it.s.pass_ms = elapsed(c, 8, 12);
+            it.s.full_eval = (mask & 1) && (!c->mixed || refresh) ? 1 : 0;
             it.a.elapsed_ms = elapsed(c, 9, 10);
             it.c.elapsed_ms = elapsed(c, 10, 11);
             it.elapsed_ms = elapsed(c, 8, 11);

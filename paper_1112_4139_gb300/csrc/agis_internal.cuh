@@ -47,22 +47,60 @@ struct __align__(16) ObsRec {
 static_assert(sizeof(ObsRec) == 64, "record must be 64 bytes");
 
 // Mixed-precision records (source order), two 32-byte halves.  MixS holds what the source
-// solve reads: the FP64 residual and the FP32 design row (A = (Ap, Aq, Aw, Ap tau, Aq tau),
-// Eq. ubardiff), sigma (negative for AC) and the weight.  MixT holds what the A and C passes
-// gather besides R and W: the attitude partial g, the descriptor and the time.
+// solve reads: the residual as an unevaluated float pair R = Rh + Rl (about 48 significant
+// bits, so that every per-observation operation runs on the FP32 pipe), the FP32 design row
+// A = (Ap, Aq, Aw, Ap tau, Aq tau) (Eq. ubardiff), sigma (negative for AC) and the weight.
+// MixT holds what the A and C passes gather besides R and W: the attitude partial g, the
+// descriptor, and the time as knot interval l with the offset u = (t - tau_l) / dt.
 struct __align__(16) MixS {
-    double R;       // residual (FP64)
+    float Rh, Rl;   // residual = Rh + Rl
     float Ap, Aq, Aw, tau;
     float sig;      // +sigma for AL, -sigma for AC
-    float W;        // w during the source solve, w / (sigma^2 + eps^2) afterwards
+    float W;        // w / (sigma^2 + eps^2) after the source update
 };
 struct __align__(16) MixT {
     float g[4];     // dR/dq / ||s||
     uint32_t meta;
+    int32_t l;      // left knot index of the observation time
+    float u;        // (t - tau_l) / knot interval
     uint32_t pad;
-    int64_t t_ns;
 };
 static_assert(sizeof(MixS) == 32 && sizeof(MixT) == 32, "mixed records must be 32 bytes");
+
+// Per-source state of the mixed S block between its kernels.
+struct __align__(16) SrcScale {
+    double s2c[2];  // sigma^2 of the AL and AC observations (one value per class)
+    double s2min;
+    float vs;       // robust scale of x = R / sigma
+    int32_t flags;  // bit 0: one sigma per class (class-sum path); bit 1: no observations
+};
+// FP32 inputs of one weight round's per-observation pass (written by the per-source solve of
+// the previous round, so that the passes need no FP64 arithmetic)
+struct __align__(16) SrcRound {
+    float dp[5];    // previous solution: the shift of the sums
+    float isd[2];   // 1 / sqrt(sigma_c^2 + eps^2_prev)
+    float sigc[2];
+    float vs;
+    int32_t mode;   // 0 first robust round, 1 later robust rounds, 2 plain weights
+    int32_t pad;
+};
+struct __align__(16) SrcFinal {  // the final update as float pairs and 1 / (sigma_c^2 + eps^2)
+    float dh[5], dl[5];
+    float iw[2];
+};
+struct RoundSums {  // FP32 class sums of one weight round, shifted to the previous solution
+    float AA[2][15];
+    float Ah[2][5];
+    float hh[2];
+    int32_t nout;
+    int32_t pad;
+};
+struct MixSrcWork {
+    SrcScale* scale;
+    SrcRound* round;
+    SrcFinal* fin;
+    RoundSums* sums;
+};
 
 // Per-source outputs of the S block (device arrays).
 struct SrcOutPtrs {

@@ -41,9 +41,8 @@ __global__ void k_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, cons
 // Constraint projection d = d~ - C (C'C)^-1 C' d~ (Eq. calCon).  The columns of C for
 // Eqs. cc1 (per interval: all 124 AL offsets) and cc3 (per interval and field: 7 AC offsets)
 // have disjoint supports, so within each column's support d = d~ - mean(d~).  One thread
-// per constraint column; then c += d (and d_cal += d where the mixed form tracks the update).
-__global__ void k_cal_project(int n_days, const double* __restrict__ dtil, double* __restrict__ cal,
-                              double* __restrict__ d_cal) {
+// per constraint column; then c += d.
+__global__ void k_cal_project(int n_days, const double* __restrict__ dtil, double* __restrict__ cal) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= 3 * n_days) return;
     int64_t k0;
@@ -59,15 +58,7 @@ __global__ void k_cal_project(int n_days, const double* __restrict__ dtil, doubl
     double s = 0.0;
     for (int i = 0; i < cnt; i++) s += dtil[k0 + i];
     const double m = s / (double)cnt;
-    for (int i = 0; i < cnt; i++) {
-        const double dk = dtil[k0 + i] - m;
-        cal[k0 + i] += dk;
-        if (d_cal) d_cal[k0 + i] += dk;
-    }
-}
-
-void launch_cal_project(int n_days, const double* dtil, double* cal, double* d_cal, cudaStream_t s) {
-    k_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal, d_cal);
+    for (int i = 0; i < cnt; i++) cal[k0 + i] += dtil[k0 + i] - m;
 }
 
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
@@ -76,7 +67,7 @@ void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* ca
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     k_cal_accum<<<blocks, 256, 0, s>>>(n_cal, perm_c, cal_off, rec, tol, dtil, rd);
-    launch_cal_project(n_days, dtil, cal, nullptr, s);
+    k_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,20 +1,30 @@
 // k_mixed.cu -- the mixed-precision form of the observation pass and of the S, A and C
-// accumulations.
+// blocks.
 //
 // Each observation keeps two 32-byte records (source order, see MixS / MixT).  A full FP64
 // evaluation of the model (k_mix_forward) refreshes R and the FP32 partials every few
 // source updates; in between, R follows the first-order identity behind Eq. precond2:
-// after the A and C blocks k_mix_correct adds (dR/da) d_a + (dR/dc) d_c, and the source
-// solve subtracts A d.  R itself stays FP64, so the updates solve for corrections of an FP64
-// residual (iterative refinement): FP32 rounding of the normal equations changes the rate
-// of convergence, not the point it converges to.  The 5x5 and band Cholesky factorisations
-// and the frame rotator stay FP64.
+// k_mix_correct adds (dR/da) d_a + (dR/dc) d_c for the A and C updates since the last source
+// update, and the source update subtracts A d.  R is kept to about 48 bits as a float pair,
+// so the updates solve for corrections of an accurately known residual (iterative
+// refinement): FP32 rounding of the normal equations changes the rate of convergence, not
+// the point it converges to.  The 5x5 and band Cholesky factorisations and the frame
+// rotator stay FP64.  Every per-observation operation runs on the FP32 pipe.
+//
+// S block: k_mix_scale_sums (sigma per class, robust scale, round-0 class sums), then per
+// weight round k_mix_solve5 (one thread per source: the 5x5 algebra of the excess-noise
+// steps in FP64) and k_mix_sums (the next round's sums), then k_mix_final (R <- R - A d and
+// W).  Sources whose sigma varies within a class take k_mix_general (all rounds in one warp
+// with per-observation sweeps).
 #include "agis_internal.cuh"
 
 namespace agis {
 
 void launch_src_geo(int32_t n_src, const double* src, double* geo, cudaStream_t s);
-void launch_cal_project(int n_days, const double* dtil, double* cal, double* d_cal, cudaStream_t s);
+
+// pivots below this fraction of N_jj are not resolved by FP32 normals: they count as zero
+// in the mixed form (App. C robust Cholesky with a tolerance for FP32 accumulation)
+constexpr double kMixPivotTol = 64.0 / 16777216.0;
 
 namespace {
 
@@ -24,11 +34,48 @@ int grid_of(int64_t n, int per_block, int cap) {
     return b < 1 ? 1 : (int)b;
 }
 
-// B_{l-3..l}(t) in FP32: closed form on regular intervals (the offset from the knot is an
-// exact integer number of ns before its conversion), Algorithm B.1 in FP64 near the end knots.
-__device__ __forceinline__ void bspline4f(const DevGeo& G, int64_t t, int l, float b[4]) {
+// ---- float-pair arithmetic (Knuth's TwoSum, FMA-based exact product) ----------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (hi, lo) += (xh, xl)
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float xh, float xl) {
+    float s, e;
+    two_sum(hi, xh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, xl));
+    fast_two_sum(s, e, hi, lo);
+}
+__device__ __forceinline__ void split_pair(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+// A d for the FP32 row A and d given as float pairs, as a float pair
+__device__ __forceinline__ void row_dot_pair(const float A[5], const float* dh, const float* dl, float& sh,
+                                             float& sl) {
+    sh = 0.0f;
+    sl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const float p = __fmul_rn(A[k], dh[k]);
+        const float e = __fmaf_rn(A[k], dh[k], -p);
+        float s, t;
+        two_sum(sh, p, s, t);
+        sh = s;
+        sl = __fadd_rn(sl, __fadd_rn(t, __fmaf_rn(A[k], dl[k], e)));
+    }
+    fast_two_sum(sh, sl, sh, sl);
+}
+
+// B_{l-3..l} at offset u (units of the knot interval) from tau_l, in FP32: closed form on
+// regular intervals, Algorithm B.1 with the knots relative to tau_l near the end knots.
+__device__ __forceinline__ void bspline4_lu(const DevGeo& G, int l, float u, float b[4]) {
     if (l >= 5 && l <= G.n_coef - 3) {
-        const float u = (float)(t - knot_at(G, l)) * (float)G.inv_knot_dt;
         const float v = 1.0f - u;
         const float u2 = u * u, u3 = u2 * u;
         b[0] = v * v * v * (1.0f / 6.0f);
@@ -37,9 +84,28 @@ __device__ __forceinline__ void bspline4f(const DevGeo& G, int64_t t, int l, flo
         b[3] = u3 * (1.0f / 6.0f);
         return;
     }
-    double bd[4];
-    bspline4(G, t, l, bd);
-    for (int j = 0; j < 4; j++) b[j] = (float)bd[j];
+    const int K = G.n_coef - 3;
+    auto kc = [K](int k) { k -= 3; return k < 0 ? 0 : (k > K ? K : k); };
+    const int k0 = kc(l);
+    float R[3], L[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        R[i] = (float)(kc(l + i + 1) - k0) - u;
+        L[i] = u - (float)(kc(l - i) - k0);
+    }
+    b[0] = 1.0f; b[1] = b[2] = b[3] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            const float den = R[j] + L[i - j];
+            const float w = den != 0.0f ? b[j] / den : 0.0f;
+            b[j] = s + R[j] * w;
+            s = L[i - j] * w;
+        }
+        b[i + 1] = s;
+    }
 }
 
 __device__ __forceinline__ float wfun_f(float z, int fn) {
@@ -68,13 +134,17 @@ __device__ __forceinline__ void arow(const MixS& r, float A[5]) {
 __device__ __forceinline__ float adot(const float A[5], const float* d) {
     return A[0] * d[0] + A[1] * d[1] + A[2] * d[2] + A[3] * d[3] + A[4] * d[4];
 }
-// A d in FP64 with the FP32 design row of the normal equations (A[3], A[4] rounded as there)
-__device__ __forceinline__ double adot_d(const MixS& r, const double* d) {
-    return (double)r.Ap * d[0] + (double)r.Aq * d[1] + (double)r.Aw * d[2] + (double)(r.Ap * r.tau) * d[3] +
-           (double)(r.Aq * r.tau) * d[4];
+
+// Weight of one observation in a round.  Round 0 (robust): w = wfun(x / vs), x = R / sigma_c;
+// later rounds: w = wfun(h' / sqrt(sigma_c^2 + y_prev)) with h' = R - A d_prev; plain: w = 1.
+// The same function serves the sums and the final pass, so both see identical weights.
+__device__ __forceinline__ float round_weight(const SrcRound& in, float Rh, float hp, int cls, int wfn) {
+    if (in.mode == 2) return 1.0f;
+    if (in.mode == 0) return in.vs > 0.0f ? wfun_f((Rh / (cls ? in.sigc[1] : in.sigc[0])) / in.vs, wfn) : 1.0f;
+    return wfun_f(hp * (cls ? in.isd[1] : in.isd[0]), wfn);
 }
 
-// ---- order statistics of x = R / sigma over a source (4-pass radix select on FP32 keys)
+// ---- order statistics of x = R / sigma over a source (4-pass radix select on FP32 keys) ----
 __device__ __forceinline__ uint32_t fkey(float x) {
     const uint32_t b = __float_as_uint(x);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -83,95 +153,105 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 __device__ __forceinline__ uint32_t xkey(const MixS* rs, int j) {
-    return fkey((float)rs[j].R / fabsf(rs[j].sig));
+    const float2 v = *reinterpret_cast<const float2*>(&rs[j].sig);
+    return fkey(rs[j].Rh / fabsf(v.x));
 }
 
-__device__ uint32_t mix_select(const MixS* rs, int n, int k, int* hist, int lane) {
-    uint32_t prefix = 0, pmask = 0;
-    int kk = k;
+// keys of one source: from a shared-memory copy when the source fits, else recomputed
+struct KeySrc {
+    const uint32_t* sk;
+    const MixS* rs;
+    __device__ __forceinline__ uint32_t operator()(int j) const { return sk ? sk[j] : xkey(rs, j); }
+};
+
+// the ka-th and kb-th smallest keys (0-based), by a 4-pass radix select with 8-bit digits in
+// which both selections share each sweep over the keys
+__device__ void select2(const KeySrc& key, int n, int ka, int kb, int* hist, int lane, uint32_t& Ka, uint32_t& Kb) {
+    uint32_t pre[2] = {0, 0}, pmask = 0;
+    int kk[2] = {ka, kb};
     for (int dgt = 3; dgt >= 0; dgt--) {
         const int shift = 8 * dgt;
 #pragma unroll
-        for (int i = 0; i < 8; i++) hist[lane * 8 + i] = 0;
+        for (int i = 0; i < 16; i++) hist[lane * 16 + i] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += kWarp) {
-            const uint32_t key = xkey(rs, j);
-            if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+            const uint32_t k = key(j);
+            const uint32_t bin = (k >> shift) & 255u;
+            if ((k & pmask) == pre[0]) atomicAdd(&hist[bin], 1);
+            if ((k & pmask) == pre[1]) atomicAdd(&hist[256 + bin], 1);
         }
         __syncwarp();
-        int c[8], tot = 0;
 #pragma unroll
-        for (int i = 0; i < 8; i++) { c[i] = hist[lane * 8 + i]; tot += c[i]; }
-        int incl = tot;
+        for (int q = 0; q < 2; q++) {
+            const int* h = hist + 256 * q;
+            int c[8], tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const unsigned ball = __ballot_sync(0xffffffffu, incl > kk);
-        const int sl = __ffs(ball) - 1;
-        int bin = 0, below = 0;
-        if (lane == sl) {
-            int acc = incl - tot, bs = 7;
+            for (int i = 0; i < 8; i++) { c[i] = h[lane * 8 + i]; tot += c[i]; }
+            int incl = tot;
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                if (acc + c[i] > kk) { bs = i; break; }
-                acc += c[i];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
             }
-            bin = lane * 8 + bs;
-            below = acc;
+            const unsigned ball = __ballot_sync(0xffffffffu, incl > kk[q]);
+            const int sl = __ffs(ball) - 1;
+            int bin = 0, below = 0;
+            if (lane == sl) {
+                int acc = incl - tot, bs = 7;
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    if (acc + c[i] > kk[q]) { bs = i; break; }
+                    acc += c[i];
+                }
+                bin = lane * 8 + bs;
+                below = acc;
+            }
+            bin = __shfl_sync(0xffffffffu, bin, sl);
+            below = __shfl_sync(0xffffffffu, below, sl);
+            kk[q] -= below;
+            pre[q] |= (uint32_t)bin << shift;
         }
-        bin = __shfl_sync(0xffffffffu, bin, sl);
-        below = __shfl_sync(0xffffffffu, below, sl);
-        kk -= below;
-        prefix |= (uint32_t)bin << shift;
         pmask |= 0xffu << shift;
         __syncwarp();
     }
-    return prefix;
+    Ka = pre[0];
+    Kb = pre[1];
 }
 
-__device__ void mix_select_pair(const MixS* rs, int n, int k, int* hist, int lane, float& v0, float& v1) {
-    const uint32_t K = mix_select(rs, n, k, hist, lane);
-    v0 = fkey_inv(K);
-    if (k + 1 >= n) { v1 = v0; return; }
-    int less = 0, eq = 0;
+// the next value after K in sorted order (K itself when the (k+1)-th smallest equals it)
+__device__ __forceinline__ float next_value(const KeySrc& key, int n, int k, uint32_t K, int lane) {
+    if (k + 1 >= n) return fkey_inv(K);
+    int le = 0;
     uint32_t nxt = 0xffffffffu;
     for (int j = lane; j < n; j += kWarp) {
-        const uint32_t key = xkey(rs, j);
-        less += key < K;
-        eq += key == K;
-        if (key > K && key < nxt) nxt = key;
+        const uint32_t v = key(j);
+        le += v <= K;
+        if (v > K && v < nxt) nxt = v;
     }
-    less = warp_sum_int(less);
-    eq = warp_sum_int(eq);
+    le = warp_sum_int(le);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const uint32_t v = __shfl_xor_sync(0xffffffffu, nxt, o);
         nxt = v < nxt ? v : nxt;
     }
-    v1 = (k + 1 < less + eq) ? v0 : fkey_inv(nxt);
+    return (k + 1 < le) ? fkey_inv(K) : fkey_inv(nxt);
 }
 
-// Robust sigma of x = R / sigma: half the distance between the 1/6 and 5/6 quantiles
-// (intersextile range, type-7 interpolation), Sect. 5.1.2.
-__device__ float mix_robust_sigma(const MixS* rs, int n, int* hist, int lane) {
+// Robust scale of x = R / sigma: half the intersextile range (type-7 interpolation), Sect. 5.1.2.
+__device__ float mix_robust_sigma(const KeySrc& key, int n, int* hist, int lane) {
     const double h1 = (1.0 / 6.0) * (double)(n - 1), h5 = (5.0 / 6.0) * (double)(n - 1);
     const int lo1 = (int)floor(h1), lo5 = (int)floor(h5);
-    float a0, a1, b0, b1;
-    mix_select_pair(rs, n, lo1, hist, lane, a0, a1);
-    mix_select_pair(rs, n, lo5, hist, lane, b0, b1);
+    uint32_t K1, K5;
+    select2(key, n, lo1, lo5, hist, lane, K1, K5);
+    const float a0 = fkey_inv(K1), a1 = next_value(key, n, lo1, K1, lane);
+    const float b0 = fkey_inv(K5), b1 = next_value(key, n, lo5, K5, lane);
     return 0.5f * ((b0 + (float)(h5 - lo5) * (b1 - b0)) - (a0 + (float)(h1 - lo1) * (a1 - a0)));
 }
 
-// ---- class sums of one source in FP32, both classes in one sweep.  The sums are shifted to
-// the previous round's solution dp: h' = R - A dp, so that Q(y) = hh - 2 d'Ah + d'AA d is
-// formed from a residual that is already small (no cancellation in FP32).
-//   mode 0: w = wfun(x / vs), x = R / sigma (initial downweighting; dp = 0)
-//   mode 1: w = wfun(h' / sqrt(sigma^2 + y_prev))
-//   mode 2: keep the stored w
-__device__ void mix_pass_class(MixS* rs, int n, int lane, int mode, float vs, const float* sigc, const float* dp,
-                               const float* isd, int wfn, ClassSums& S, int& nout) {
+// Class sums of one source for one round (whole warp), shifted to the previous solution:
+// h' = R - A dp, so that Q(y) = hh - 2 d'Ah + d'AA d is formed without cancellation.
+__device__ __forceinline__ void class_sums(const MixS* rs, int n, int lane, const SrcRound& in, int wfn,
+                                           RoundSums* out) {
     float AA[2][15], Ah[2][5], hh[2] = {0.0f, 0.0f};
 #pragma unroll
     for (int c = 0; c < 2; c++) {
@@ -185,21 +265,11 @@ __device__ void mix_pass_class(MixS* rs, int n, int lane, int mode, float vs, co
         const MixS r = rs[j];
         float A[5];
         arow(r, A);
-        const bool ac = r.sig < 0.0f;
-        const float m1 = ac ? 1.0f : 0.0f, m0 = 1.0f - m1;
-        const float h = (float)r.R - adot(A, dp);
-        float w;
-        if (mode == 0) {
-            w = vs > 0.0f ? wfun_f(((float)r.R / (ac ? sigc[1] : sigc[0])) / vs, wfn) : 1.0f;
-            rs[j].W = w;
-        } else if (mode == 1) {
-            w = wfun_f(h * (ac ? isd[1] : isd[0]), wfn);
-            rs[j].W = w;
-        } else {
-            w = r.W;
-        }
+        const int cls = r.sig < 0.0f ? 1 : 0;
+        const float hp = r.Rh - adot(A, in.dp);
+        const float w = round_weight(in, r.Rh, hp, cls, wfn);
         cnt += (w < 0.2f);
-        const float w0 = w * m0, w1 = w * m1;
+        const float w1 = cls ? w : 0.0f, w0 = w - w1;
 #pragma unroll
         for (int a = 0; a < 5; a++) {
             const float wa0 = w0 * A[a], wa1 = w1 * A[a];
@@ -208,11 +278,11 @@ __device__ void mix_pass_class(MixS* rs, int n, int lane, int mode, float vs, co
                 AA[0][up5(a, b)] = fmaf(wa0, A[b], AA[0][up5(a, b)]);
                 AA[1][up5(a, b)] = fmaf(wa1, A[b], AA[1][up5(a, b)]);
             }
-            Ah[0][a] = fmaf(wa0, h, Ah[0][a]);
-            Ah[1][a] = fmaf(wa1, h, Ah[1][a]);
+            Ah[0][a] = fmaf(wa0, hp, Ah[0][a]);
+            Ah[1][a] = fmaf(wa1, hp, Ah[1][a]);
         }
-        hh[0] = fmaf(w0 * h, h, hh[0]);
-        hh[1] = fmaf(w1 * h, h, hh[1]);
+        hh[0] = fmaf(w0 * hp, hp, hh[0]);
+        hh[1] = fmaf(w1 * hp, hp, hh[1]);
     }
 #pragma unroll
     for (int c = 0; c < 2; c++) {
@@ -222,24 +292,27 @@ __device__ void mix_pass_class(MixS* rs, int n, int lane, int mode, float vs, co
         for (int i = 0; i < 5; i++) Ah[c][i] = warp_sum_f(Ah[c][i]);
         hh[c] = warp_sum_f(hh[c]);
     }
-    nout = warp_sum_int(cnt);
-    if (lane == 0) {
+    cnt = warp_sum_int(cnt);
+    // lanes write disjoint parts of the 176-byte record
+    float* o = reinterpret_cast<float*>(out);
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
+    for (int c = 0; c < 2; c++) {
 #pragma unroll
-            for (int i = 0; i < 15; i++) S.AA[c][i] = AA[c][i];
+        for (int i = 0; i < 15; i++)
+            if (lane == ((c * 15 + i) & 31)) o[c * 15 + i] = AA[c][i];
 #pragma unroll
-            for (int i = 0; i < 5; i++) S.Ah[c][i] = Ah[c][i];
-            S.hh[c] = hh[c];
-        }
+        for (int i = 0; i < 5; i++)
+            if (lane == ((30 + c * 5 + i) & 31)) o[30 + c * 5 + i] = Ah[c][i];
     }
-    __syncwarp();
+    if (lane == 8) o[40] = hh[0];
+    if (lane == 9) o[41] = hh[1];
+    if (lane == 10) out->nout = cnt;
 }
 
 // ---- general path (sigma varies within a class): per-observation sweeps for every
 // excess-noise step, FP32 sums shifted to the previous round's solution.
-__device__ __forceinline__ void mix_gen_normals(MixS* rs, int n, int lane, float y, bool refresh, const float* dp,
-                                                float yp, int wfn, double* N, double* b, int& nout) {
+__device__ __forceinline__ void gen_normals(MixS* rs, int n, int lane, float y, bool refresh, const float* dp,
+                                            float yp, int wfn, double* N, double* b, int& nout) {
     float Nf[15], bf[5];
 #pragma unroll
     for (int i = 0; i < 15; i++) Nf[i] = 0.0f;
@@ -251,7 +324,7 @@ __device__ __forceinline__ void mix_gen_normals(MixS* rs, int n, int lane, float
         float A[5];
         arow(r, A);
         const float s2 = r.sig * r.sig;
-        const float h = (float)r.R - adot(A, dp);
+        const float h = r.Rh - adot(A, dp);
         float w = r.W;
         if (refresh) {
             w = wfun_f(h / sqrtf(s2 + yp), wfn);
@@ -274,15 +347,14 @@ __device__ __forceinline__ void mix_gen_normals(MixS* rs, int n, int lane, float
     nout = warp_sum_int(cnt);
 }
 
-// Q(y) = sum w R^2 / (sigma^2 + y) and S2 = sum w R^2 / (sigma^2 + y)^2 for R = h' - A delta
-__device__ __forceinline__ void mix_gen_q(const MixS* rs, int n, int lane, const float* dp, const float* dl, float y,
-                                          double& Q, double& S2) {
+__device__ __forceinline__ void gen_q(const MixS* rs, int n, int lane, const float* dp, const float* dl, float y,
+                                      double& Q, double& S2) {
     float q = 0.0f, s = 0.0f;
     for (int j = lane; j < n; j += kWarp) {
         const MixS r = rs[j];
         float A[5];
         arow(r, A);
-        const float R = ((float)r.R - adot(A, dp)) - adot(A, dl);
+        const float R = (r.Rh - adot(A, dp)) - adot(A, dl);
         const float den = r.sig * r.sig + y;
         const float t = r.W * R * R / den;
         q += t;
@@ -292,12 +364,50 @@ __device__ __forceinline__ void mix_gen_q(const MixS* rs, int n, int lane, const
     S2 = (double)warp_sum_f(s);
 }
 
-__device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n, const double* s5, double cosd,
-                                               MixS* rs, double s2min, float vs, const SrcOutPtrs& out, int lane) {
+// R <- R - A d and the chi^2 term, for one record (float-pair arithmetic)
+__device__ __forceinline__ float apply_update(MixS* r, const MixS& v, const float* dh, const float* dl, float W) {
+    float A[5];
+    arow(v, A);
+    float sh, sl;
+    row_dot_pair(A, dh, dl, sh, sl);
+    float Rh = v.Rh, Rl = v.Rl;
+    pair_add(Rh, Rl, -sh, -sl);
+    *reinterpret_cast<float4*>(r) = make_float4(Rh, Rl, v.Ap, v.Aq);
+    r->W = W;
+    return W * Rh * Rh;
+}
+
+__device__ __forceinline__ void write_source(const SrcOutPtrs& out, int i, const double* d, const double* U, double y,
+                                             double Q0, int nu, int nout, int rd) {
+    double* sp = out.src + 5 * (size_t)i;
+    const double cosd = cos(sp[1]);
+    sp[0] += d[0] / cosd;
+    sp[1] += d[1];
+    sp[2] += d[2];
+    sp[3] += d[3];
+    sp[4] += d[4];
+    for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
+    for (int c = 0; c < 5; c++) {
+        double e[5] = {0, 0, 0, 0, 0};
+        e[c] = 1.0;
+        double x[5];
+        chol5_solve(U, e, x);
+        for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
+    }
+    out.eps2[i] = y;
+    out.nu[i] = nu;
+    out.nout[i] = nout;
+    out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
+    out.rankdef[i] = rd;
+}
+
+__device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n, MixS* rs, double s2min, float vs,
+                                               const SrcOutPtrs& out, int lane) {
+    const double tol_piv = fmax(st.pivot_tol, kMixPivotTol);
     if (st.robust) {
         for (int j = lane; j < n; j += kWarp) {
             const MixS r = rs[j];
-            rs[j].W = vs > 0.0f ? wfun_f(((float)r.R / fabsf(r.sig)) / vs, st.weight_fn) : 1.0f;
+            rs[j].W = vs > 0.0f ? wfun_f((r.Rh / fabsf(r.sig)) / vs, st.weight_fn) : 1.0f;
         }
     } else {
         for (int j = lane; j < n; j += kWarp) rs[j].W = 1.0f;
@@ -313,61 +423,41 @@ __device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n,
         const float yp = (float)y;
         double N[15], b[5], dl[5];
         y = 0.0;
-        mix_gen_normals(rs, n, lane, 0.0f, rnd > 0, dpf, yp, st.weight_fn, N, b, nout);
+        gen_normals(rs, n, lane, 0.0f, rnd > 0, dpf, yp, st.weight_fn, N, b, nout);
         nu = n - nout - 5;
-        rd = chol5(N, U, st.pivot_tol);
+        rd = chol5(N, U, tol_piv);
         chol5_solve(U, b, dl);
         float dlf[5] = {(float)dl[0], (float)dl[1], (float)dl[2], (float)dl[3], (float)dl[4]};
-        mix_gen_q(rs, n, lane, dpf, dlf, 0.0f, Q, S2);
+        gen_q(rs, n, lane, dpf, dlf, 0.0f, Q, S2);
         Q0 = Q;
         if (st.robust && nu > 0 && Q0 > (double)nu) {
             const double tol = 1e-12 * s2min;
             for (int it = 0; it < st.n_eps; it++) {
                 const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
                 y = fmax(0.0, y + dy);
-                mix_gen_normals(rs, n, lane, (float)y, false, dpf, yp, st.weight_fn, N, b, nout);
-                rd = chol5(N, U, st.pivot_tol);
+                gen_normals(rs, n, lane, (float)y, false, dpf, yp, st.weight_fn, N, b, nout);
+                rd = chol5(N, U, tol_piv);
                 chol5_solve(U, b, dl);
                 for (int a = 0; a < 5; a++) dlf[a] = (float)dl[a];
-                mix_gen_q(rs, n, lane, dpf, dlf, (float)y, Q, S2);
+                gen_q(rs, n, lane, dpf, dlf, (float)y, Q, S2);
                 if (fabs(dy) <= tol) break;
             }
         }
         for (int a = 0; a < 5; a++) d[a] = (double)dpf[a] + dl[a];
         __syncwarp();
     }
-    double chi = 0.0;
+    float dh[5], dlo[5];
+    for (int a = 0; a < 5; a++) split_pair(d[a], dh[a], dlo[a]);
+    float chi = 0.0f;
     for (int j = lane; j < n; j += kWarp) {
         const MixS v = rs[j];
-        const double R = v.R - adot_d(v, d);
-        const float W = v.W / (v.sig * v.sig + (float)y);
-        rs[j].R = R;
-        rs[j].W = W;
-        chi += (double)W * R * R;
+        chi += apply_update(rs + j, v, dh, dlo, v.W / (v.sig * v.sig + (float)y));
     }
-    chi = warp_sum(chi);
+    const double chid = warp_sum((double)chi);
     if (lane == 0) {
-        double* sp = out.src + 5 * (size_t)i;
-        sp[0] = s5[0] + d[0] / cosd;
-        sp[1] = s5[1] + d[1];
-        sp[2] = s5[2] + d[2];
-        sp[3] = s5[3] + d[3];
-        sp[4] = s5[4] + d[4];
-        for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
-        for (int c = 0; c < 5; c++) {
-            double e[5] = {0, 0, 0, 0, 0};
-            e[c] = 1.0;
-            double x[5];
-            chol5_solve(U, e, x);
-            for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
-        }
-        out.eps2[i] = y;
-        out.q[i] = chi;
-        out.nu[i] = nu;
-        out.nout[i] = nout;
-        out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
-        out.chi2[i] = chi;
-        out.rankdef[i] = rd;
+        write_source(out, i, d, U, y, Q0, nu, nout, rd);
+        out.q[i] = chid;
+        out.chi2[i] = chid;
     }
     __syncwarp();
 }
@@ -394,7 +484,7 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
         ObsOut ob;
         observe<true>(G, S, t, m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
         MixS a;
-        a.R = ob.R;
+        split_pair(ob.R, a.Rh, a.Rl);
         a.Ap = (float)ob.A[0];
         a.Aq = (float)ob.A[1];
         a.Aw = (float)ob.A[2];
@@ -405,8 +495,9 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
         MixT b;
         for (int k = 0; k < 4; k++) b.g[k] = (float)ob.g[k];
         b.meta = m;
+        b.l = left_index(G, t);
+        b.u = (float)((double)(t - knot_at(G, b.l)) * G.inv_knot_dt);
         b.pad = 0;
-        b.t_ns = t;
         mt[o] = b;
     }
 }
@@ -414,343 +505,343 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
 // R += sum_j B_j g . d_a[l-3+j] + d_c[k]  (dR/da_n = g B_n, dR/dc_k = 1; Eqs. dfadq, pdC)
 __global__ void __launch_bounds__(256) k_mix_correct(DevGeo G, int64_t n_obs, MixS* __restrict__ ms,
                                                      const MixT* __restrict__ mt, const float4* __restrict__ d_att,
-                                                     const double* __restrict__ d_cal) {
+                                                     const float2* __restrict__ d_cal) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
         const MixT r = mt[o];
-        const int l = left_index(G, r.t_ns);
         float B[4];
-        bspline4f(G, r.t_ns, l, B);
-        const float4* da = d_att + (l - 3);
+        bspline4_lu(G, r.l, r.u, B);
+        const float4* da = d_att + (r.l - 3);
         float corr = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const float4 v = __ldg(da + j);
             corr = fmaf(B[j], r.g[0] * v.x + r.g[1] * v.y + r.g[2] * v.z + r.g[3] * v.w, corr);
         }
-        ms[o].R += (double)corr + __ldg(d_cal + meta_cal(r.meta));
+        const float2 dc = __ldg(d_cal + meta_cal(r.meta));
+        float2 R = *reinterpret_cast<const float2*>(ms + o);
+        pair_add(R.x, R.y, dc.x, dc.y);
+        pair_add(R.x, R.y, corr, 0.0f);
+        *reinterpret_cast<float2*>(ms + o) = R;
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// per-source solve: batches of sources per warp as in the FP64 form; lane k solves source
-// k's 5x5 systems in FP64 from the FP32 class sums
+// S block
 // ---------------------------------------------------------------------------------------
-constexpr int kMixWarps = 2;
-__global__ void __launch_bounds__(32 * kMixWarps) k_mix_solve(Settings st, const int64_t* __restrict__ src_off,
-                                                              const int32_t* __restrict__ src_order, int32_t n_src,
-                                                              int batch, SrcOutPtrs out, MixS* __restrict__ ms,
-                                                              int* work_counter) {
-    __shared__ int hist_all[kMixWarps * 256];
-    __shared__ ClassSums sums_all[kMixWarps][kWarp];
+constexpr int kScaleWarps = 4;
+constexpr int kKeyCap = 1536;  // keys of a source kept in shared memory (6 KB per warp)
+
+// sigma per class, robust scale and the round-0 class sums; one warp per source (largest first)
+__global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st, const int64_t* __restrict__ src_off,
+                                                                     const int32_t* __restrict__ src_order,
+                                                                     int32_t n_src, const MixS* __restrict__ ms,
+                                                                     MixSrcWork w) {
+    __shared__ int hist_all[kScaleWarps][512];
+    __shared__ uint32_t keys_all[kScaleWarps][kKeyCap];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    int* hist = hist_all + wib * 256;
-    ClassSums* sums = sums_all[wib];
-    const int rounds = st.robust ? st.n_rounds + 1 : 1;
-    for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(work_counter, batch);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_src) break;
-        const int nb = min(batch, n_src - base);
-        const bool mine = lane < nb;
-        const int my_i = mine ? src_order[base + lane] : 0;
-        const int64_t my_o0 = mine ? src_off[my_i] : 0;
-        const int my_n = mine ? (int)(src_off[my_i + 1] - my_o0) : 0;
-        double s5[5] = {0, 0, 0, 0, 0};
-        if (mine)
-            for (int k = 0; k < 5; k++) s5[k] = out.src[5 * (size_t)my_i + k];
-        const double cosd = cos(s5[1]);
-        double my_s2c[2] = {1.0, 1.0}, my_s2min = 1.0;
-        float my_vs = 0.0f;
-        bool my_uniform = false;
-        // ---- per source: sigma per class (one value per class selects the class-sum path)
-        for (int k = 0; k < nb; k++) {
-            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
-            const int n = __shfl_sync(0xffffffffu, my_n, k);
-            if (n == 0) continue;
-            const MixS* rs = ms + o0;
-            float lo[2] = {3.0e38f, 3.0e38f}, hi[2] = {0.0f, 0.0f};
-            for (int j = lane; j < n; j += kWarp) {
-                const float sg = rs[j].sig;
-                const float a = fabsf(sg);
-                if (sg < 0.0f) { lo[1] = fminf(lo[1], a); hi[1] = fmaxf(hi[1], a); }
-                else { lo[0] = fminf(lo[0], a); hi[0] = fmaxf(hi[0], a); }
+    int* hist = hist_all[wib];
+    uint32_t* skeys = keys_all[wib];
+    const int nw = gridDim.x * kScaleWarps;
+    for (int q = blockIdx.x * kScaleWarps + wib; q < n_src; q += nw) {
+        const int i = src_order[q];
+        const int64_t o0 = src_off[i];
+        const int n = (int)(src_off[i + 1] - o0);
+        if (n == 0) {
+            if (lane == 0) {
+                SrcScale sc;
+                sc.s2c[0] = sc.s2c[1] = sc.s2min = 1.0;
+                sc.vs = 0.0f;
+                sc.flags = 2;
+                w.scale[i] = sc;
             }
-#pragma unroll
-            for (int c = 0; c < 2; c++)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-                    hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-                }
-            const bool has0 = hi[0] > 0.0f, has1 = hi[1] > 0.0f;
-            const bool uni = (!has0 || lo[0] == hi[0]) && (!has1 || lo[1] == hi[1]);
-            const float vs = st.robust ? mix_robust_sigma(rs, n, hist, lane) : 0.0f;
-            if (lane == k) {
-                my_uniform = uni;
-                my_s2c[0] = has0 ? (double)lo[0] * (double)lo[0] : 1.0;
-                my_s2c[1] = has1 ? (double)lo[1] * (double)lo[1] : 1.0;
-                const float smin = fminf(lo[0], lo[1]);
-                my_s2min = (double)smin * (double)smin;
-                my_vs = vs;
-            }
+            continue;
         }
-        // ---- inner iteration, class-sum path
-        double d[5] = {0, 0, 0, 0, 0};
-        double U[15];
-        for (int q = 0; q < 15; q++) U[q] = 0.0;
-        double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
-        int nu = 0, nout = 0, rd = 0;
-        for (int rnd = 0; rnd < rounds; rnd++) {
-            // the shift: the previous round's solution rounded to FP32 (it is applied as such)
-            double dp[5];
-            for (int a = 0; a < 5; a++) dp[a] = (double)(float)d[a];
-            for (int k = 0; k < nb; k++) {
-                const int n = __shfl_sync(0xffffffffu, my_n, k);
-                const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
-                if (n == 0 || !uni) continue;
-                const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
-                float dk[5];
-                for (int a = 0; a < 5; a++) dk[a] = (float)__shfl_sync(0xffffffffu, dp[a], k);
-                const double yk = __shfl_sync(0xffffffffu, y, k);
-                const double s2c[2] = {__shfl_sync(0xffffffffu, my_s2c[0], k), __shfl_sync(0xffffffffu, my_s2c[1], k)};
-                const float vsk = __shfl_sync(0xffffffffu, my_vs, k);
-                const float sigc[2] = {(float)sqrt(s2c[0]), (float)sqrt(s2c[1])};
-                const float isd[2] = {(float)(1.0 / sqrt(s2c[0] + yk)), (float)(1.0 / sqrt(s2c[1] + yk))};
-                MixS* rs = ms + o0;
-                int no = 0;
-                if (!st.robust) {
-                    if (rnd == 0) {
-                        for (int j = lane; j < n; j += kWarp) rs[j].W = 1.0f;
-                        __syncwarp();
-                    }
-                    mix_pass_class(rs, n, lane, 2, 0.0f, sigc, dk, isd, st.weight_fn, sums[k], no);
-                } else {
-                    mix_pass_class(rs, n, lane, rnd == 0 ? 0 : 1, vsk, sigc, dk, isd, st.weight_fn, sums[k], no);
-                }
-                if (lane == k) nout = no;
-            }
-            __syncwarp();
-            if (mine && my_n > 0 && my_uniform) {
-                double dl[5];
-                nu = my_n - nout - 5;
-                y = 0.0;
-                class_solve(sums[lane], my_s2c, 0.0, st.pivot_tol, U, dl, rd, Q, S2);
-                Q0 = Q;
-                if (st.robust && nu > 0 && Q0 > (double)nu) {
-                    const double tol = 1e-12 * my_s2min;
-                    for (int it = 0; it < st.n_eps; it++) {
-                        const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
-                        y = fmax(0.0, y + dy);
-                        class_solve(sums[lane], my_s2c, y, st.pivot_tol, U, dl, rd, Q, S2);
-                        if (fabs(dy) <= tol) break;
-                    }
-                }
-                for (int a = 0; a < 5; a++) d[a] = dp[a] + dl[a];
-            }
-            __syncwarp();
-        }
-        // ---- residuals after the update (FP64) and the statistical weights
-        double my_chi = 0.0;
-        for (int k = 0; k < nb; k++) {
-            const int n = __shfl_sync(0xffffffffu, my_n, k);
-            const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
-            if (n == 0 || !uni) continue;
-            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
-            double dk[5];
-            for (int a = 0; a < 5; a++) dk[a] = __shfl_sync(0xffffffffu, d[a], k);
-            const double yk = __shfl_sync(0xffffffffu, y, k);
-            const float iw[2] = {(float)(1.0 / (__shfl_sync(0xffffffffu, my_s2c[0], k) + yk)),
-                                 (float)(1.0 / (__shfl_sync(0xffffffffu, my_s2c[1], k) + yk))};
-            MixS* rs = ms + o0;
-            double chi = 0.0;
-            for (int j = lane; j < n; j += kWarp) {
-                const MixS v = rs[j];
-                const double R = v.R - adot_d(v, dk);
-                const float W = v.W * iw[v.sig < 0.0f ? 1 : 0];
-                rs[j].R = R;
-                rs[j].W = W;
-                chi += (double)W * R * R;
-            }
-            chi = warp_sum(chi);
-            if (lane == k) my_chi = chi;
-        }
-        if (mine && (my_n == 0 || my_uniform)) {
-            const int i = my_i;
-            if (my_n == 0) {
-                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = 0.0;
-                for (int k = 0; k < 25; k++) out.cov[25 * (size_t)i + k] = 0.0;
-                out.eps2[i] = out.q[i] = out.dsig[i] = out.chi2[i] = 0.0;
-                out.nu[i] = out.nout[i] = out.rankdef[i] = 0;
+        const MixS* rs = ms + o0;
+        const bool in_smem = n <= kKeyCap;
+        float lo[2] = {3.0e38f, 3.0e38f}, hi[2] = {0.0f, 0.0f};
+        for (int j = lane; j < n; j += kWarp) {
+            const float2 v = *reinterpret_cast<const float2*>(&rs[j].sig);
+            const float sg = v.x;
+            if (in_smem) skeys[j] = fkey(rs[j].Rh / fabsf(sg));
+            if (sg < 0.0f) {
+                lo[1] = fminf(lo[1], -sg);
+                hi[1] = fmaxf(hi[1], -sg);
             } else {
-                double* sp = out.src + 5 * (size_t)i;
-                sp[0] = s5[0] + d[0] / cosd;
-                sp[1] = s5[1] + d[1];
-                sp[2] = s5[2] + d[2];
-                sp[3] = s5[3] + d[3];
-                sp[4] = s5[4] + d[4];
-                for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = d[k];
-                for (int c = 0; c < 5; c++) {
-                    double e[5] = {0, 0, 0, 0, 0};
-                    e[c] = 1.0;
-                    double x[5];
-                    chol5_solve(U, e, x);
-                    for (int k = 0; k < 5; k++) out.cov[25 * (size_t)i + 5 * k + c] = x[k];
-                }
-                out.eps2[i] = y;
-                out.q[i] = my_chi;  // Q at the final (d, eps^2), from the FP64 residuals
-                out.nu[i] = nu;
-                out.nout[i] = nout;
-                out.dsig[i] = nu > 0 ? (Q0 - (double)nu) / sqrt(2.0 * (double)nu) : 0.0;
-                out.chi2[i] = my_chi;
-                out.rankdef[i] = rd;
+                lo[0] = fminf(lo[0], sg);
+                hi[0] = fmaxf(hi[0], sg);
             }
         }
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+                hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+            }
         __syncwarp();
-        // ---- sources without one sigma per class
-        for (int k = 0; k < nb; k++) {
-            const int n = __shfl_sync(0xffffffffu, my_n, k);
-            const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
-            if (n == 0 || uni) continue;
-            const int i = __shfl_sync(0xffffffffu, my_i, k);
-            const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
-            double sk[5];
-            for (int a = 0; a < 5; a++) sk[a] = __shfl_sync(0xffffffffu, s5[a], k);
-            const double ck = __shfl_sync(0xffffffffu, cosd, k);
-            const double s2m = __shfl_sync(0xffffffffu, my_s2min, k);
-            const float vsk = __shfl_sync(0xffffffffu, my_vs, k);
-            mix_solve_general(st, i, n, sk, ck, ms + o0, s2m, vsk, out, lane);
+        const bool has0 = hi[0] > 0.0f, has1 = hi[1] > 0.0f;
+        const bool uni = (!has0 || lo[0] == hi[0]) && (!has1 || lo[1] == hi[1]);
+        const KeySrc key{in_smem ? skeys : nullptr, rs};
+        SrcRound in;
+        for (int a = 0; a < 5; a++) in.dp[a] = 0.0f;
+        in.isd[0] = in.isd[1] = 0.0f;
+        in.sigc[0] = has0 ? lo[0] : 1.0f;
+        in.sigc[1] = has1 ? lo[1] : 1.0f;
+        in.vs = st.robust ? mix_robust_sigma(key, n, hist, lane) : 0.0f;
+        in.mode = st.robust ? 0 : 2;
+        in.pad = 0;
+        if (lane == 0) {
+            SrcScale sc;
+            sc.s2c[0] = has0 ? (double)lo[0] * (double)lo[0] : 1.0;
+            sc.s2c[1] = has1 ? (double)lo[1] * (double)lo[1] : 1.0;
+            const float smin = fminf(lo[0], lo[1]);
+            sc.s2min = (double)smin * (double)smin;
+            sc.vs = in.vs;
+            sc.flags = uni ? 1 : 0;
+            w.scale[i] = sc;
+            w.round[i] = in;
+        }
+        if (uni) class_sums(rs, n, lane, in, st.weight_fn, w.sums + i);
+        __syncwarp();
+    }
+}
+
+// class sums of round r >= 1 (weights and shift from the previous round's solution)
+constexpr int kSumWarps = 4;
+__global__ void __launch_bounds__(32 * kSumWarps) k_mix_sums(Settings st, const int64_t* __restrict__ src_off,
+                                                             const int32_t* __restrict__ src_order, int32_t n_src,
+                                                             const MixS* __restrict__ ms, MixSrcWork w) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kSumWarps;
+    for (int q = blockIdx.x * kSumWarps + (threadIdx.x >> 5); q < n_src; q += nw) {
+        const int i = src_order[q];
+        if (w.scale[i].flags != 1) continue;
+        const int64_t o0 = src_off[i];
+        const int n = (int)(src_off[i + 1] - o0);
+        const SrcRound in = w.round[i];
+        class_sums(ms + o0, n, lane, in, st.weight_fn, w.sums + i);
+    }
+}
+
+// the 5x5 algebra of one round, one thread per source: N(y), b(y), Q(y) from the class sums,
+// y = 0 first, then the rational steps of the excess variance; d = d_prev + delta.  Writes the
+// FP32 inputs of the next round, or after the last round the final update and the outputs.
+__global__ void __launch_bounds__(128) k_mix_solve5(Settings st, int last, const int64_t* __restrict__ src_off,
+                                                    int32_t n_src, SrcOutPtrs out, MixSrcWork w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_src) return;
+    const SrcScale sc = w.scale[i];
+    if (sc.flags & 2) {
+        if (last) {
+            for (int k = 0; k < 5; k++) out.d[5 * (size_t)i + k] = 0.0;
+            for (int k = 0; k < 25; k++) out.cov[25 * (size_t)i + k] = 0.0;
+            out.eps2[i] = out.q[i] = out.dsig[i] = out.chi2[i] = 0.0;
+            out.nu[i] = out.nout[i] = out.rankdef[i] = 0;
+        }
+        return;
+    }
+    if (!(sc.flags & 1)) return;
+    const int n = (int)(src_off[i + 1] - src_off[i]);
+    const RoundSums& rsum = w.sums[i];
+    ClassSums S;
+    for (int c = 0; c < 2; c++) {
+        for (int k = 0; k < 15; k++) S.AA[c][k] = rsum.AA[c][k];
+        for (int k = 0; k < 5; k++) S.Ah[c][k] = rsum.Ah[c][k];
+        S.hh[c] = rsum.hh[c];
+    }
+    const int nout = rsum.nout;
+    SrcRound in = w.round[i];
+    const double tol_piv = fmax(st.pivot_tol, kMixPivotTol);
+    double U[15], dl[5], Q, S2;
+    int rd;
+    const int nu = n - nout - 5;
+    double y = 0.0;
+    class_solve(S, sc.s2c, 0.0, tol_piv, U, dl, rd, Q, S2);
+    const double Q0 = Q;
+    if (st.robust && nu > 0 && Q0 > (double)nu) {
+        const double tol = 1e-12 * sc.s2min;
+        for (int it = 0; it < st.n_eps; it++) {
+            const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
+            y = fmax(0.0, y + dy);
+            class_solve(S, sc.s2c, y, tol_piv, U, dl, rd, Q, S2);
+            if (fabs(dy) <= tol) break;
+        }
+    }
+    double d[5];
+    for (int a = 0; a < 5; a++) d[a] = (double)in.dp[a] + dl[a];
+    if (!last) {
+        for (int a = 0; a < 5; a++) in.dp[a] = (float)d[a];
+        for (int c = 0; c < 2; c++) in.isd[c] = (float)(1.0 / sqrt(sc.s2c[c] + y));
+        in.mode = 1;
+        w.round[i] = in;
+    } else {
+        SrcFinal f;
+        for (int a = 0; a < 5; a++) split_pair(d[a], f.dh[a], f.dl[a]);
+        for (int c = 0; c < 2; c++) f.iw[c] = (float)(1.0 / (sc.s2c[c] + y));
+        w.fin[i] = f;
+        write_source(out, i, d, U, y, Q0, nu, nout, rd);
+    }
+}
+
+// R <- R - A d (float pairs), W = w / (sigma_c^2 + eps^2) with the last round's weights, chi^2
+__global__ void __launch_bounds__(32 * kSumWarps) k_mix_final(Settings st, const int64_t* __restrict__ src_off,
+                                                              const int32_t* __restrict__ src_order, int32_t n_src,
+                                                              SrcOutPtrs out, MixS* __restrict__ ms, MixSrcWork w) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kSumWarps;
+    for (int q = blockIdx.x * kSumWarps + (threadIdx.x >> 5); q < n_src; q += nw) {
+        const int i = src_order[q];
+        if (w.scale[i].flags != 1) continue;
+        const int64_t o0 = src_off[i];
+        const int n = (int)(src_off[i + 1] - o0);
+        const SrcRound in = w.round[i];
+        const SrcFinal f = w.fin[i];
+        MixS* rs = ms + o0;
+        float chi = 0.0f;
+        for (int j = lane; j < n; j += kWarp) {
+            const MixS v = rs[j];
+            float A[5];
+            arow(v, A);
+            const int cls = v.sig < 0.0f ? 1 : 0;
+            const float wgt = round_weight(in, v.Rh, v.Rh - adot(A, in.dp), cls, st.weight_fn);
+            chi += apply_update(rs + j, v, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]));
+        }
+        chi = warp_sum_f(chi);
+        if (lane == 0) {
+            out.chi2[i] = chi;
+            out.q[i] = chi;  // Q at the final (d, eps^2)
         }
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// A block accumulation with FP32 arithmetic (same staging as the FP64 form): per knot
-// interval the 16x16 block W (B B') (x) (g g' + 4 lambda^2 s s') and the right-hand side
-// -W B (x) (R g [- 2 lambda^2 D s]) (Eqs. normAmod, dDldan).
-//
-// The sums are compensated (Knuth's TwoSum: hi + lo carries the sum to about 2^-48 relative)
-// because the attitude normals are nearly singular along the coefficient vector itself:
-// the observation terms vanish along it (g is orthogonal to q) and only the norm term of
-// relative size 4 lambda^2 ~ 4e-6 fixes it, which plain FP32 accumulation (2^-24 per
-// addition, growing with the number of terms) does not resolve.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
-    const float s = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    hi = s;
-    lo = __fadd_rn(lo, e);
+__global__ void __launch_bounds__(32 * kSumWarps) k_mix_general(Settings st, const int64_t* __restrict__ src_off,
+                                                                int32_t n_src, SrcOutPtrs out, MixS* __restrict__ ms,
+                                                                MixSrcWork w) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kSumWarps;
+    for (int i = blockIdx.x * kSumWarps + (threadIdx.x >> 5); i < n_src; i += nw) {
+        const SrcScale sc = w.scale[i];
+        if (sc.flags != 0) continue;
+        const int64_t o0 = src_off[i];
+        const int n = (int)(src_off[i + 1] - o0);
+        mix_solve_general(st, i, n, ms + o0, sc.s2min, sc.vs, out, lane);
+    }
 }
 
-__host__ __device__ constexpr int mtri16(int i, int j) { return i * 16 - i * (i - 1) / 2 + (j - i); }
-__host__ __device__ constexpr int mtri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
-constexpr int kMStage = 28;  // B[4], M[10], r[4], BB[10]
+// ---------------------------------------------------------------------------------------
+// A block accumulation (Eqs. normAmod, dDldan), one warp per knot interval.  Each lane
+// sums its own observations in FP32 registers: the 100 distinct products BB'[p] M[m] of
+// the 16x16 block (p, m over the 10 upper entries of the 4x4 matrices B B' and
+// M = W (g g' + 4 lambda^2 s s')) and the 16 products B r.  The 32 lane partials are then
+// added with TwoSum (compensated), because the attitude normals are nearly singular along
+// the coefficient vector: the observation terms vanish along it (g is orthogonal to q) and
+// only the norm term of relative size 4 lambda^2 fixes it.
+// ---------------------------------------------------------------------------------------
+constexpr int kAccVals = 116;
+constexpr int kAccPad = 117;
+constexpr int kAttWarps = 2;
 
-__global__ void __launch_bounds__(128) k_mix_att_accum(DevGeo G, float lambda2, int rhs_norm,
-                                                       const uint32_t* __restrict__ perm_t,
-                                                       const int64_t* __restrict__ ivl_off, int n_iv,
-                                                       const MixS* __restrict__ ms, const MixT* __restrict__ mt,
-                                                       const double* __restrict__ att, double* __restrict__ blk) {
-    __shared__ float stage_all[4][kWarp * kMStage];
+__host__ __device__ constexpr int mtri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
+__host__ __device__ constexpr int mtri16(int i, int j) { return i * 16 - i * (i - 1) / 2 + (j - i); }
+static_assert(mtri16(15, 15) == 135 && mtri16(1, 1) == 16, "upper-triangle index of the 16x16 block");
+
+__global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, float lambda2, int rhs_norm,
+                                                                  const uint32_t* __restrict__ perm_t,
+                                                                  const int64_t* __restrict__ ivl_off, int n_iv,
+                                                                  const MixS* __restrict__ ms,
+                                                                  const MixT* __restrict__ mt,
+                                                                  const double* __restrict__ att,
+                                                                  double* __restrict__ blk) {
+    __shared__ float red_all[kAttWarps][kWarp * kAccPad];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    float* stg = stage_all[wib];
-    int oi[5], oj[5];
+    float* red = red_all[wib];
+    // the accumulator index of each of this lane's (up to 5) block outputs o = lane + 32 k
+    int src_idx[5];
+    float sgn[5];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         const int o = lane + 32 * k;
-        oi[k] = -1; oj[k] = -1;
+        src_idx[k] = -1;
+        sgn[k] = 1.0f;
         if (o < 136) {
             int i = 0;
             while (o >= mtri16(i, 15) + 1) i++;
-            oi[k] = i;
-            oj[k] = i + (o - mtri16(i, i));
+            const int j = i + (o - mtri16(i, i));
+            const int bi = i >> 2, ci = i & 3, bj = j >> 2, cj = j & 3;
+            const int m = ci <= cj ? mtri4(ci, cj) : mtri4(cj, ci);
+            src_idx[k] = mtri4(bi, bj) * 10 + m;
         } else if (o < kBlkVals) {
-            oi[k] = o - 136;
+            src_idx[k] = 100 + (o - 136);
+            sgn[k] = -1.0f;
         }
     }
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int iv = blockIdx.x * (blockDim.x >> 5) + wib; iv < n_iv; iv += nwarps) {
+    const int nwarps = gridDim.x * kAttWarps;
+    const float l4 = 4.0f * lambda2;
+    for (int iv = blockIdx.x * kAttWarps + wib; iv < n_iv; iv += nwarps) {
         const int l = iv + 3;
-        const double* ad = att + 4 * (int64_t)(l - 3);
+        // the 16 coefficients of the interval: one conversion per lane, then broadcast
+        const float af = lane < 16 ? (float)att[4 * (int64_t)(l - 3) + lane] : 0.0f;
         float a[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++) a[k] = (float)ad[k];
-        float acc[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+        for (int k = 0; k < 16; k++) a[k] = __shfl_sync(0xffffffffu, af, k);
+        float acc[kAccVals];
+#pragma unroll
+        for (int k = 0; k < kAccVals; k++) acc[k] = 0.0f;
         const int64_t beg = ivl_off[iv], end = ivl_off[iv + 1];
-        for (int64_t base = beg; base < end; base += kWarp) {
-            const int64_t j = base + lane;
-            float* st = stg + lane * kMStage;
-            if (j < end) {
-                const uint32_t o = perm_t[j];
-                const MixT rt = mt[o];
-                const MixS rs = ms[o];
-                const float W = rs.W;
-                const float Rf = (float)rs.R;
-                float B[4];
-                bspline4f(G, rt.t_ns, l, B);
-                float s[4];
+        for (int64_t j = beg + lane; j < end; j += kWarp) {
+            const uint32_t o = perm_t[j];
+            const MixT rt = mt[o];
+            const float2 RW = make_float2(ms[o].Rh, ms[o].W);
+            float B[4];
+            bspline4_lu(G, l, rt.u, B);
+            float s[4];
 #pragma unroll
-                for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
-                const float l4 = 4.0f * lambda2;
+            for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
+            const float W = RW.y;
+            float M[10], r[4], BB[10];
 #pragma unroll
-                for (int c = 0; c < 4; c++)
+            for (int c = 0; c < 4; c++)
 #pragma unroll
-                    for (int e = c; e < 4; e++) st[4 + mtri4(c, e)] = W * (rt.g[c] * rt.g[e] + l4 * s[c] * s[e]);
-                float D = 0.0f;
-                if (rhs_norm) {
-                    // 1 - |s|^2 cancels: form it in FP64
-                    double Bd[4];
-                    bspline4(G, rt.t_ns, l, Bd);
-                    double sd2 = 0.0;
-                    for (int c = 0; c < 4; c++) {
-                        const double v = Bd[0] * ad[c] + Bd[1] * ad[4 + c] + Bd[2] * ad[8 + c] + Bd[3] * ad[12 + c];
-                        sd2 += v * v;
-                    }
-                    D = (float)(1.0 - sd2);
+                for (int e = c; e < 4; e++) {
+                    M[mtri4(c, e)] = W * (rt.g[c] * rt.g[e] + l4 * s[c] * s[e]);
+                    BB[mtri4(c, e)] = B[c] * B[e];
                 }
+            float D = 0.0f;
+            if (rhs_norm) D = 1.0f - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    float v = Rf * rt.g[c];
-                    if (rhs_norm) v -= 2.0f * lambda2 * D * s[c];
-                    st[14 + c] = W * v;
-                    st[c] = B[c];
-                }
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-#pragma unroll
-                    for (int e = c; e < 4; e++) st[18 + mtri4(c, e)] = B[c] * B[e];
-            } else {
-#pragma unroll
-                for (int c = 0; c < kMStage; c++) st[c] = 0.0f;
+            for (int c = 0; c < 4; c++) {
+                float v = RW.x * rt.g[c];
+                if (rhs_norm) v -= 2.0f * lambda2 * D * s[c];
+                r[c] = W * v;
             }
-            __syncwarp();
-            const int cnt = (int)((end - base) < kWarp ? (end - base) : kWarp);
-            for (int q = 0; q < cnt; q++) {
-                const float* sq = stg + q * kMStage;
 #pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    if (oi[k] < 0) continue;
-                    const int i = oi[k];
-                    if (oj[k] >= 0) {
-                        const int jj = oj[k];
-                        const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
-                        const int mi = ci <= cj ? mtri4(ci, cj) : mtri4(cj, ci);
-                        two_sum_acc(acc[k], lo[k], __fmul_rn(sq[18 + mtri4(bi, bj)], sq[4 + mi]));
-                    } else {
-                        two_sum_acc(acc[k], lo[k], -__fmul_rn(sq[i >> 2], sq[14 + (i & 3)]));
-                    }
-                }
-            }
-            __syncwarp();
+            for (int p = 0; p < 10; p++)
+#pragma unroll
+                for (int m = 0; m < 10; m++) acc[p * 10 + m] = fmaf(BB[p], M[m], acc[p * 10 + m]);
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[100 + 4 * b + c] = fmaf(B[b], r[c], acc[100 + 4 * b + c]);
         }
+        // compensated cross-lane reduction through shared memory
+#pragma unroll
+        for (int k = 0; k < kAccVals; k++) red[lane * kAccPad + k] = acc[k];
+        __syncwarp();
 #pragma unroll
         for (int k = 0; k < 5; k++) {
-            const int o = lane + 32 * k;
-            if (o < kBlkVals) blk[(int64_t)iv * kBlkVals + o] = (double)acc[k] + (double)lo[k];
+            if (src_idx[k] < 0) continue;
+            float hi = 0.0f, lo = 0.0f;
+            for (int q = 0; q < kWarp; q++) {
+                float s_, e_;
+                two_sum(hi, red[q * kAccPad + src_idx[k]], s_, e_);
+                hi = s_;
+                lo = __fadd_rn(lo, e_);
+            }
+            blk[(int64_t)iv * kBlkVals + lane + 32 * k] = (double)sgn[k] * ((double)hi + (double)lo);
         }
+        __syncwarp();
     }
 }
 
@@ -761,19 +852,19 @@ __global__ void k_mix_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, 
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_cal; k += nw) {
-        double sw = 0.0, swr = 0.0;
+        float sw = 0.0f, swr = 0.0f;
         for (int64_t j = cal_off[k] + lane; j < cal_off[k + 1]; j += kWarp) {
-            const MixS r = ms[perm_c[j]];
-            const double W = (double)r.W;
+            const MixS* r = ms + perm_c[j];
+            const float W = r->W;
             sw += W;
-            swr += W * r.R;
+            swr = fmaf(W, r->Rh, swr);
         }
-        sw = warp_sum(sw);
-        swr = warp_sum(swr);
+        const double swd = warp_sum((double)sw);
+        const double swrd = warp_sum((double)swr);
         if (lane == 0) {
-            if (sw > 0.0) {
-                const double u = sqrt(sw);
-                dtil[k] = (-swr / u) / u;
+            if (swd > 0.0) {
+                const double u = sqrt(swd);
+                dtil[k] = (-swrd / u) / u;
                 rd[k] = 0;
             } else {
                 dtil[k] = 0.0;
@@ -783,9 +874,37 @@ __global__ void k_mix_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, 
     }
 }
 
+// constraint projection as in the FP64 form (Eq. calCon: disjoint groups, d = d~ - mean d~);
+// c += d, and the update is accumulated as a float pair for the next linearized pass
+__global__ void k_mix_cal_project(int n_days, const double* __restrict__ dtil, double* __restrict__ cal,
+                                  float2* __restrict__ d_cal) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= 3 * n_days) return;
+    int64_t k0;
+    int cnt;
+    if (g < n_days) {
+        k0 = (int64_t)g * 124;
+        cnt = 124;
+    } else {
+        k0 = (int64_t)n_days * 124 + (int64_t)(g - n_days) * 7;
+        cnt = 7;
+    }
+    double s = 0.0;
+    for (int i = 0; i < cnt; i++) s += dtil[k0 + i];
+    const double m = s / (double)cnt;
+    for (int i = 0; i < cnt; i++) {
+        const double dk = dtil[k0 + i] - m;
+        cal[k0 + i] += dk;
+        const float2 p = d_cal[k0 + i];
+        float hi, lo;
+        split_pair((double)p.x + (double)p.y + dk, hi, lo);
+        d_cal[k0 + i] = make_float2(hi, lo);
+    }
+}
+
 __global__ void k_mix_rw(int64_t n, const MixS* __restrict__ ms, double* __restrict__ R, double* __restrict__ W) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        if (R) R[o] = ms[o].R;
+        if (R) R[o] = (double)ms[o].Rh + (double)ms[o].Rl;
         if (W) W[o] = (double)ms[o].W;
     }
 }
@@ -793,13 +912,14 @@ __global__ void k_mix_rw(int64_t n, const MixS* __restrict__ ms, double* __restr
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
-void launch_mix_s(const DevGeo& G, const Settings& st, bool refresh, const int64_t* t_ns, const uint32_t* meta,
-                  const float* sigma, const double* mu, const int32_t* obs_src, int64_t n_obs, const int64_t* src_off,
-                  const int32_t* src_order, int32_t n_src, const double* att, const double* cal, const SrcOutPtrs& out,
-                  MixS* ms, MixT* mt, double* geo, float* d_att, double* d_cal, int n_coef, int n_cal, int* work,
-                  cudaStream_t s) {
+// the observation pass of the mixed S block: the full FP64 model (refresh) or the linearized
+// correction by the A and C updates since the last source update; both leave d_att, d_cal zero
+void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+                     const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
+                     const double* att, const double* cal, MixS* ms, MixT* mt, double* geo, float* d_att,
+                     float2* d_cal, int n_coef, int n_cal, cudaStream_t s) {
     if (refresh) {
-        launch_src_geo(n_src, out.src, geo, s);
+        launch_src_geo(n_src, src, geo, s);
         k_mix_forward<<<grid_of(n_obs, 256, 152 * 64), 256, 0, s>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo,
                                                                      att, cal, ms, mt);
     } else {
@@ -807,26 +927,35 @@ void launch_mix_s(const DevGeo& G, const Settings& st, bool refresh, const int64
                                                                      reinterpret_cast<const float4*>(d_att), d_cal);
     }
     cudaMemsetAsync(d_att, 0, sizeof(float) * 4 * (size_t)n_coef, s);
-    cudaMemsetAsync(d_cal, 0, sizeof(double) * (size_t)n_cal, s);
-    cudaMemsetAsync(work, 0, sizeof(int), s);
-    int batch = n_src / (152 * 16);
-    batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
-    const int warps = (n_src + batch - 1) / batch;
-    k_mix_solve<<<grid_of(warps, kMixWarps, 152 * 32), 32 * kMixWarps, 0, s>>>(st, src_off, src_order, n_src, batch,
-                                                                                out, ms, work);
+    cudaMemsetAsync(d_cal, 0, sizeof(float2) * (size_t)n_cal, s);
+}
+
+void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_order, int32_t n_src,
+                      const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s) {
+    const int rounds = st.robust ? st.n_rounds + 1 : 1;
+    const int warp_blocks = grid_of(n_src, kSumWarps, 152 * 16);
+    const int thread_blocks = (n_src + 127) / 128 > 0 ? (n_src + 127) / 128 : 1;
+    k_mix_scale_sums<<<grid_of(n_src, kScaleWarps, 152 * 8), 32 * kScaleWarps, 0, s>>>(st, src_off, src_order, n_src,
+                                                                                       ms, w);
+    for (int r = 0; r < rounds; r++) {
+        if (r > 0) k_mix_sums<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_order, n_src, ms, w);
+        k_mix_solve5<<<thread_blocks, 128, 0, s>>>(st, r == rounds - 1, src_off, n_src, out, w);
+    }
+    k_mix_final<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_order, n_src, out, ms, w);
+    k_mix_general<<<grid_of(n_src, kSumWarps, 152 * 4), 32 * kSumWarps, 0, s>>>(st, src_off, n_src, out, ms, w);
 }
 
 void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
                           const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
                           double* blk, cudaStream_t s) {
-    k_mix_att_accum<<<grid_of(n_iv, 4, 152 * 32), 128, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t, ivl_off, n_iv,
-                                                               ms, mt, att, blk);
+    k_mix_att_accum<<<grid_of(n_iv, kAttWarps, 152 * 64), 32 * kAttWarps, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t,
+                                                                                 ivl_off, n_iv, ms, mt, att, blk);
 }
 
 void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
-                    double* dtil, int* rd, double* cal, double* d_cal, cudaStream_t s) {
+                    double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s) {
     k_mix_cal_accum<<<grid_of(n_cal, 8, 152 * 16), 256, 0, s>>>(n_cal, perm_c, cal_off, ms, dtil, rd);
-    launch_cal_project(n_days, dtil, cal, d_cal, s);
+    k_mix_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal, d_cal);
 }
 
 void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s) {

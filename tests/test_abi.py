@@ -1,4 +1,5 @@
 """The C-ABI library loads and exports every symbol that include/agis.h declares (no GPU needed)."""
+import ctypes as C
 import os
 import re
 
@@ -23,10 +24,12 @@ def test_library_builds_and_exports_all_declared_symbols():
     assert declared == set(agis.EXPORTS)
     for name in declared:
         assert hasattr(lib, name), name
-    assert lib.agis_abi_version() == 1
+    assert lib.agis_abi_version() == agis.ABI_VERSION == 2
 
 
 def test_default_config_and_struct_sizes():
+    assert C.sizeof(agis.BlockStats) == 104 and C.sizeof(agis.IterStats) == 3 * 104 + 56
     cfg = agis.default_config()
+    assert cfg.precision == 0 and cfg.refresh_every == 8
     assert cfg.robust == 1 and cfg.n_rounds == 4 and cfg.n_eps == 3 and abs(cfg.lambda_att - 1e-3) < 1e-18
     assert cfg.seg_overlap == 12 and cfg.pivot_tol == 1e-12
