@@ -495,29 +495,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     // device geometry
     DevGeo& G = c->G;
-    std::memset(&G, 0, sizeof(G));
-    G.gamma_half = 0.5 * geo->gamma_c;
-    G.F = geo->focal_length;
-    G.p_ac = geo->p_ac;
-    G.mu_c = geo->mu_c;
-    for (int i = 0; i < AGIS_N_CCD; i++) {
-        G.eta0[i] = geo->eta0[i];
-        G.x_fpa[i] = geo->x_fpa[i];
-    }
-    G.x_centre[0] = geo->x_centre[0];
-    G.x_centre[1] = geo->x_centre[1];
-    G.orb_L0 = geo->orb_L0;
-    G.cos_obl = std::cos(geo->obliquity);
-    G.sin_obl = std::sin(geo->obliquity);
-    G.au_light_s = geo->au_light_s;
-    G.year_s = geo->year_s;
-    G.orb_rate = 2.0 * 3.141592653589793 / geo->year_s;
-    G.t_ep_ns = geo->t_ep_ns;
-    G.t_fr_ns = geo->t_fr_ns;
-    G.knot0_ns = geo->knot0_ns;
-    G.knot_dt_ns = geo->knot_dt_ns;
-    G.inv_knot_dt = 1.0 / (double)geo->knot_dt_ns;
-    G.n_coef = n_coef;
+    fill_devgeo(geo, n_coef, G);
     Settings& st = c->st;
     st.robust = cfg->robust;
     st.n_rounds = cfg->n_rounds;

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <cstring>
+
 #include "agis.h"
 
 namespace agis {
@@ -25,15 +28,49 @@ __host__ __device__ inline uint32_t meta_cal(uint32_t m) { return m >> 8; }
 // Geometry passed by value to the kernels.
 struct DevGeo {
     double gamma_half;
+    double cos_gh, sin_gh;       // cos and sin of gamma_half
     double F, p_ac, mu_c;
     double eta0[kNccd];
     double x_fpa[kNccd];
     double x_centre[2];
     double orb_L0, cos_obl, sin_obl, au_light_s, year_s, orb_rate;
+    double orb_L0_pi, inv_year_s, vk;   // L0 / pi, 1 / year, orbital speed / c
     int64_t t_ep_ns, t_fr_ns, knot0_ns, knot_dt_ns;
     double inv_knot_dt;
     int32_t n_coef;
 };
+
+inline void fill_devgeo(const agis_geometry* geo, int32_t n_coef, DevGeo& G) {
+    const double pi = 3.141592653589793;
+    std::memset(&G, 0, sizeof(G));
+    G.gamma_half = 0.5 * geo->gamma_c;
+    G.cos_gh = std::cos(G.gamma_half);
+    G.sin_gh = std::sin(G.gamma_half);
+    G.F = geo->focal_length;
+    G.p_ac = geo->p_ac;
+    G.mu_c = geo->mu_c;
+    for (int i = 0; i < kNccd; i++) {
+        G.eta0[i] = geo->eta0[i];
+        G.x_fpa[i] = geo->x_fpa[i];
+    }
+    G.x_centre[0] = geo->x_centre[0];
+    G.x_centre[1] = geo->x_centre[1];
+    G.orb_L0 = geo->orb_L0;
+    G.cos_obl = std::cos(geo->obliquity);
+    G.sin_obl = std::sin(geo->obliquity);
+    G.au_light_s = geo->au_light_s;
+    G.year_s = geo->year_s;
+    G.orb_rate = 2.0 * pi / geo->year_s;
+    G.orb_L0_pi = geo->orb_L0 / pi;
+    G.inv_year_s = 1.0 / geo->year_s;
+    G.vk = G.orb_rate * geo->au_light_s;
+    G.t_ep_ns = geo->t_ep_ns;
+    G.t_fr_ns = geo->t_fr_ns;
+    G.knot0_ns = geo->knot0_ns;
+    G.knot_dt_ns = geo->knot_dt_ns;
+    G.inv_knot_dt = 1.0 / (double)geo->knot_dt_ns;
+    G.n_coef = n_coef;
+}
 
 // Hand-over record written by the S pass and read (gathered) by the A and C passes.
 struct __align__(16) ObsRec {
@@ -218,12 +255,24 @@ __device__ __forceinline__ void qmul(const double* a, const double* b, double* c
     c[3] = -a[0] * b[0] - a[1] * b[1] - a[2] * b[2] + a[3] * b[3];
 }
 
-// attitude matrix of a unit quaternion, Eq. quat2mat (rows: SRS axes in the ICRS)
-__device__ __forceinline__ void quat2mat(const double* q, double m[9]) {
-    double x = q[0], y = q[1], z = q[2], w = q[3];
-    m[0] = 1.0 - 2.0 * (y * y + z * z); m[1] = 2.0 * (x * y + z * w); m[2] = 2.0 * (x * z - y * w);
-    m[3] = 2.0 * (x * y - z * w); m[4] = 1.0 - 2.0 * (x * x + z * z); m[5] = 2.0 * (y * z + x * w);
-    m[6] = 2.0 * (x * z + y * w); m[7] = 2.0 * (y * z - x * w); m[8] = 1.0 - 2.0 * (x * x + y * y);
+// |s|^2 times the attitude matrix of the quaternion s / |s| (Eq. quat2mat in homogeneous
+// form; rows: SRS axes in the ICRS).  The field angles are invariant to the scale.
+__device__ __forceinline__ void quat2mat_h(const double* q, double m[9]) {
+    const double x = q[0], y = q[1], z = q[2], w = q[3];
+    const double xx = x * x, yy = y * y, zz = z * z, ww = w * w;
+    m[0] = ww + xx - yy - zz; m[1] = 2.0 * (x * y + z * w); m[2] = 2.0 * (x * z - y * w);
+    m[3] = 2.0 * (x * y - z * w); m[4] = ww - xx + yy - zz; m[5] = 2.0 * (y * z + x * w);
+    m[6] = 2.0 * (x * z + y * w); m[7] = 2.0 * (y * z - x * w); m[8] = ww - xx - yy + zz;
+}
+
+// atan2(y, x) for a direction within 0.02 rad of the x axis by the Taylor series of arctan
+// (the remainder after the t^9 term is below 2e-20 rad); atan2 elsewhere.
+__device__ __forceinline__ double atan2_small(double y, double x) {
+    if (x > 0.0 && fabs(y) <= 0.02 * x) {
+        const double t = y / x, t2 = t * t;
+        return t * (1.0 + t2 * (-1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (-1.0 / 7.0 + t2 * (1.0 / 9.0)))));
+    }
+    return atan2(y, x);
 }
 
 // Per-source geometry: normal triad (Eq. normal-triad) and the parameters.
@@ -256,89 +305,93 @@ struct ObsOut {
 //   source partials: Eqs. srspqr, srsprop1diffsol, ubardiff, duds (evaluated in the ICRS by
 //   turning m and n back with the attitude matrix)
 //   attitude partials: Eq. dfadq divided by ||s|| (normalisation of Eq. qspline)
+// The field angles depend on the direction only, so neither the aberrated direction nor the
+// attitude quaternion is normalised: the rotation uses |s|^2 R(s/|s|), and the along-scan
+// angle is measured from the field centre after turning by -f Gamma / 2.
 template <bool kPartials>
 __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_t t, uint32_t meta, double mu,
                                         const double* __restrict__ att, const double* __restrict__ cal,
                                         ObsOut& o) {
-    // ephemeris: circular orbit, ICRS components (AU, AU/s)
-    double ts = (double)t * 1e-9;
-    double Lang = G.orb_L0 + 2.0 * 3.141592653589793 * (ts / G.year_s);
+    // ephemeris: circular orbit, ICRS components (AU, AU/s in units of c); L = pi x
     double sL, cL;
-    sincos(Lang, &sL, &cL);
-    double b[3] = {cL, G.cos_obl * sL, G.sin_obl * sL};
-    double vc[3] = {-G.orb_rate * sL * G.au_light_s, G.cos_obl * G.orb_rate * cL * G.au_light_s,
-                    G.sin_obl * G.orb_rate * cL * G.au_light_s};
+    sincospi(G.orb_L0_pi + 2.0 * ((double)t * 1e-9) * G.inv_year_s, &sL, &cL);
+    const double b[3] = {cL, G.cos_obl * sL, G.sin_obl * sL};
+    const double vc[3] = {-G.vk * sL, G.vk * G.cos_obl * cL, G.vk * G.sin_obl * cL};
     // Roemer delay and proper-motion time
-    double rb = dot3(S.r, b);
-    double tau = ((double)(t - G.t_ep_ns) * 1e-9 + rb * G.au_light_s) / G.year_s;
+    const double rb = dot3(S.r, b);
+    const double tau = ((double)(t - G.t_ep_ns) * 1e-9 + rb * G.au_light_s) * G.inv_year_s;
     double ub[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) ub[i] = S.r[i] + tau * (S.p[i] * S.pma + S.q[i] * S.pmd) - S.par * b[i];
-    double nb = sqrt(dot3(ub, ub));
-    ub[0] /= nb; ub[1] /= nb; ub[2] /= nb;
-    double u[3] = {ub[0] + vc[0], ub[1] + vc[1], ub[2] + vc[2]};
-    double nu = sqrt(dot3(u, u));
-    u[0] /= nu; u[1] /= nu; u[2] /= nu;
+    const double inb = 1.0 / sqrt(dot3(ub, ub));
+    ub[0] *= inb; ub[1] *= inb; ub[2] *= inb;
+    const double u[3] = {ub[0] + vc[0], ub[1] + vc[1], ub[2] + vc[2]};
     // attitude
-    int l = left_index(G, t);
+    const int l = left_index(G, t);
     double B[4];
     bspline4(G, t, l, B);
     const double* a = att + 4 * (int64_t)(l - 3);
     double s[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
-    double ns = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
-    double q[4] = {s[0] / ns, s[1] / ns, s[2] / ns, s[3] / ns};
     double Am[9];
-    quat2mat(q, Am);
-    double us[3] = {dot3(Am, u), dot3(Am + 3, u), dot3(Am + 6, u)};
-    double phi = atan2(us[1], us[0]);
-    double rho = sqrt(us[0] * us[0] + us[1] * us[1]);
-    double zeta = atan2(us[2], rho);
-    uint32_t fov = meta_fov(meta), kind = meta_kind(meta), ccd = meta_ccd(meta);
-    double f = fov == 0 ? 1.0 : -1.0;
-    double c_k = cal[meta_cal(meta)];
+    quat2mat_h(s, Am);
+    const double us[3] = {dot3(Am, u), dot3(Am + 3, u), dot3(Am + 6, u)};
+    const uint32_t fov = meta_fov(meta), kind = meta_kind(meta), ccd = meta_ccd(meta);
+    const double f = fov == 0 ? 1.0 : -1.0;
+    const double c_k = cal[meta_cal(meta)];
+    const double rho2 = us[0] * us[0] + us[1] * us[1];
+    const double irho = rsqrt(rho2);
+    const double zeta = atan2_small(us[2], rho2 * irho);
     if (kind == 0) {
-        double eta = phi - f * G.gamma_half;
-        o.R = (G.eta0[ccd] + c_k) - eta;
+        // eta = phi - f Gamma/2 from the direction turned by -f Gamma/2 about the z axis
+        const double c0 = G.cos_gh * us[0] + f * G.sin_gh * us[1];
+        const double c1 = G.cos_gh * us[1] - f * G.sin_gh * us[0];
+        o.R = (G.eta0[ccd] + c_k) - atan2_small(c1, c0);
     } else {
-        double zeta0 = -(G.x_fpa[ccd] - (mu - G.mu_c) * G.p_ac - G.x_centre[fov]) / G.F;
+        const double zeta0 = -(G.x_fpa[ccd] - (mu - G.mu_c) * G.p_ac - G.x_centre[fov]) / G.F;
         o.R = (zeta0 + c_k) - zeta;
     }
     if (!kPartials) return;
-    // m, n in the SRS (Eq. srspqr) from the components of S'u
-    double cphi = us[0] / rho, sphi = us[1] / rho;
-    double czeta = rho, szeta = us[2];
-    double ms[3] = {-sphi, cphi, 0.0};
-    double nsv[3] = {-szeta * cphi, -szeta * sphi, czeta};
-    // back to the ICRS: x_C = A' x_S
+    // m, n in the SRS (Eq. srspqr)
+    const double cphi = us[0] * irho, sphi = us[1] * irho;
+    double czeta, szeta;
+    if (fabs(zeta) <= 0.02) {
+        const double z2 = zeta * zeta;
+        czeta = 1.0 + z2 * (-0.5 + z2 * (1.0 / 24.0 + z2 * (-1.0 / 720.0)));
+        szeta = zeta * (1.0 + z2 * (-1.0 / 6.0 + z2 * (1.0 / 120.0 + z2 * (-1.0 / 5040.0))));
+    } else {
+        const double in = rsqrt(rho2 + us[2] * us[2]);
+        czeta = rho2 * irho * in;
+        szeta = us[2] * in;
+    }
+    const double ms[3] = {-sphi, cphi, 0.0};
+    const double nsv[3] = {-szeta * cphi, -szeta * sphi, czeta};
+    // back to the ICRS: x_C = R' x_S with R = Am / |s|^2
+    const double ins2 = 1.0 / (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
     const double* e = (kind == 0) ? ms : nsv;
-    double ec[3] = {Am[0] * e[0] + Am[3] * e[1] + Am[6] * e[2], Am[1] * e[0] + Am[4] * e[1] + Am[7] * e[2],
-                    Am[2] * e[0] + Am[5] * e[1] + Am[8] * e[2]};
+    const double ec[3] = {(Am[0] * e[0] + Am[3] * e[1] + Am[6] * e[2]) * ins2,
+                          (Am[1] * e[0] + Am[4] * e[1] + Am[7] * e[2]) * ins2,
+                          (Am[2] * e[0] + Am[5] * e[1] + Am[8] * e[2]) * ins2};
     // du/ds' = [(1 - ub'v/c) I - ub v'/c] dub/ds'  (Eq. duds); e'du = (1-ubv) e'x - (e'ub)(v'x)
-    double ubv = dot3(ub, vc);
-    double eub = dot3(ec, ub);
-    double dpar[3] = {-(b[0] - S.r[0] * rb), -(b[1] - S.r[1] * rb), -(b[2] - S.r[2] * rb)};
-    double sc = (kind == 0) ? 1.0 / czeta : 1.0;
-    double Ap = ((1.0 - ubv) * dot3(ec, S.p) - eub * dot3(vc, S.p)) * sc;
-    double Aq = ((1.0 - ubv) * dot3(ec, S.q) - eub * dot3(vc, S.q)) * sc;
-    double Aw = ((1.0 - ubv) * dot3(ec, dpar) - eub * dot3(vc, dpar)) * sc;
+    const double ubv = dot3(ub, vc);
+    const double eub = dot3(ec, ub);
+    const double dpar[3] = {-(b[0] - S.r[0] * rb), -(b[1] - S.r[1] * rb), -(b[2] - S.r[2] * rb)};
+    const double secz = 1.0 / czeta;
+    const double sc = (kind == 0) ? secz : 1.0;
+    const double Ap = ((1.0 - ubv) * dot3(ec, S.p) - eub * dot3(vc, S.p)) * sc;
+    const double Aq = ((1.0 - ubv) * dot3(ec, S.q) - eub * dot3(vc, S.q)) * sc;
+    const double Aw = ((1.0 - ubv) * dot3(ec, dpar) - eub * dot3(vc, dpar)) * sc;
     o.A[0] = Ap; o.A[1] = Aq; o.A[2] = Aw; o.A[3] = Ap * tau; o.A[4] = Aq * tau;
     o.tau = tau;
-    // attitude: dR_AL/dq = 2 sec(zeta) q {n,0};  dR_AC/dq = -2 q {m,0}
-    double v4[4];
-    double gq[4];
-    if (kind == 0) {
-        v4[0] = nsv[0]; v4[1] = nsv[1]; v4[2] = nsv[2]; v4[3] = 0.0;
-        qmul(q, v4, gq);
-        double k2 = 2.0 / czeta / ns;
-        o.g[0] = gq[0] * k2; o.g[1] = gq[1] * k2; o.g[2] = gq[2] * k2; o.g[3] = gq[3] * k2;
-    } else {
-        v4[0] = ms[0]; v4[1] = ms[1]; v4[2] = ms[2]; v4[3] = 0.0;
-        qmul(q, v4, gq);
-        double k2 = -2.0 / ns;
-        o.g[0] = gq[0] * k2; o.g[1] = gq[1] * k2; o.g[2] = gq[2] * k2; o.g[3] = gq[3] * k2;
-    }
+    // attitude: dR_AL/dq = 2 sec(zeta) q {n,0};  dR_AC/dq = -2 q {m,0}; divided by ||s||, with
+    // q = s / ||s||: g = k qmul(s, {e,0}) / ||s||^2
+    double v4[4], gq[4];
+    const double* w3 = (kind == 0) ? nsv : ms;
+    v4[0] = w3[0]; v4[1] = w3[1]; v4[2] = w3[2]; v4[3] = 0.0;
+    qmul(s, v4, gq);
+    const double k2 = ((kind == 0) ? 2.0 * secz : -2.0) * ins2;
+    o.g[0] = gq[0] * k2; o.g[1] = gq[1] * k2; o.g[2] = gq[2] * k2; o.g[3] = gq[3] * k2;
 }
 
 // ---------------------------------------------------------------------------------------
