@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--refresh-every", type=int, default=8, help="mixed form: full FP64 evaluation period")
     ap.add_argument("--single-form", action="store_true", help="time only the --precision form")
     ap.add_argument("--knot-dt-s", type=int, default=0, help="override the attitude knot interval (testing)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="wall time to 1 uas RMS of both forms against an FP64 reference solution")
+    ap.add_argument("--ref-max-iter", type=int, default=160, help="convergence: cap of the FP64 reference run")
+    ap.add_argument("--ref-tol-uas", type=float, default=1e-3, help="convergence: reference stops below this update")
     return ap.parse_args()
 
 
@@ -260,6 +264,92 @@ def time_form(agis, ds, stream, cfg, steps, warmup, local, dist):
             "solve_ms": med([it["s"]["elapsed_ms"] - it["s"]["pass_ms"] for it in its])}
 
 
+def run_convergence(args, agis, ds, stream, rank):
+    """Wall time to 1 uas RMS (all sources, 5 parameters, uas and uas/yr) of each form against
+    x_ref, the FP64 solution iterated until its largest update is below --ref-tol-uas (or
+    --ref-max-iter iterations).  Both runs rotate the frame onto the same reference every
+    iteration.  Iteration times are device time (CUDA events around each iteration); the
+    read-back of the sources for the monitoring is not counted."""
+    import synth
+    UAS = synth.UAS
+    seg_len = 2880 if ds.geometry["knot_dt_ns"] <= 30_000_000_000 else 720
+    ref = np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]])
+    cosd = np.cos(ds.src_true[:, 1])
+
+    def diff_uas(a, b):
+        e = a - b
+        e[:, 0] = (np.mod(e[:, 0] + np.pi, 2 * np.pi) - np.pi) * cosd
+        return e / UAS
+
+    def open_form(prec):
+        cfg = agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, precision=prec,
+                                  refresh_every=args.refresh_every)
+        obs_d = agis.obs_from_dataset(ds, device="cuda")
+        return agis.Agis(ds.geometry, cfg, obs_d, np.ascontiguousarray(ds.src0), np.ascontiguousarray(ds.att0),
+                         np.ascontiguousarray(ds.cal0), src_ref=ref, stream=stream.cuda_stream)
+
+    # FP64 reference trajectory: per-iteration updates kept as FP32 differences in uas
+    g = open_form(0)
+    prev = g.sources()
+    deltas, t64 = [], []
+    k = 0
+    while k < args.ref_max_iter:
+        its = g.iterate(1)
+        t64.append(its[0]["elapsed_ms"])
+        cur = g.sources()
+        dlt = diff_uas(cur, prev)
+        deltas.append(dlt.astype(np.float32))
+        prev = cur
+        k += 1
+        if np.max(np.abs(dlt)) < args.ref_tol_uas:
+            break
+    x_ref = prev
+    ref_last_update = float(np.max(np.abs(deltas[-1])))
+    g.close()
+    # RMS of x_k - x_ref from the stored updates, backwards
+    tail = np.zeros_like(deltas[0], dtype=np.float64)
+    rms64 = [0.0] * len(deltas)
+    for j in range(len(deltas) - 1, -1, -1):
+        rms64[j] = float(np.sqrt(np.mean(tail ** 2)))
+        tail += deltas[j]
+    del deltas
+
+    def first_below(rms, times, thr=1.0):
+        for j, v in enumerate(rms):
+            if v <= thr:
+                return j + 1, float(np.sum(times[:j + 1])) * 1e-3
+        return None, None
+
+    it64, s64 = first_below(rms64, t64)
+    # mixed form against the same reference
+    g = open_form(1)
+    rmsm, tm = [], []
+    for k in range(args.ref_max_iter):
+        its = g.iterate(1)
+        tm.append(its[0]["elapsed_ms"])
+        e = diff_uas(g.sources(), x_ref)
+        rmsm.append(float(np.sqrt(np.mean(e ** 2))))
+        if rmsm[-1] <= 1.0:
+            per_param = np.sqrt(np.mean(e ** 2, axis=0)).tolist()
+            break
+    else:
+        per_param = None
+    g.close()
+    itm, sm = first_below(rmsm, tm)
+    line = {"metric": "wall time to 1 uas RMS vs FP64 reference", "unit": "s", "higher_is_better": False,
+            "workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs, "n_src": ds.n_src,
+            "reference": {"form": "fp64", "iterations": len(rms64), "last_max_update_uas": ref_last_update,
+                          "tol_uas": args.ref_tol_uas},
+            "fp64": {"iterations": it64, "seconds": s64, "ms_per_iter": float(np.median(t64)),
+                     "rms_uas": [round(v, 4) for v in rms64[:it64 or len(rms64)]]},
+            "mixed": {"iterations": itm, "seconds": sm, "ms_per_iter": float(np.median(tm)),
+                      "refresh_every": args.refresh_every, "rms_uas": [round(v, 4) for v in rmsm],
+                      "per_param_rms_uas_at_1uas": per_param},
+            "speedup": (s64 / sm) if (s64 and sm) else None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -278,6 +368,8 @@ def main():
     from paper_1112_4139_gb300 import agis
     ds, t_gen = make_dataset(args)
     stream = torch.cuda.Stream()
+    if args.convergence:
+        return run_convergence(args, agis, ds, stream, rank)
     seg_len = 2880 if ds.geometry["knot_dt_ns"] <= 30_000_000_000 else 720
     forms = {"fp64": dict(precision=0), "mixed": dict(precision=1, refresh_every=args.refresh_every)}
     head = args.precision
