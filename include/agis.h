@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 2
+#define AGIS_ABI_VERSION 3
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -120,7 +120,11 @@ typedef struct agis_block_stats {
 typedef struct agis_iter_stats {
     agis_block_stats s, a, c;
     double frame[6];             /* (eps, omega) applied by the frame rotator            */
-    double elapsed_ms;
+    double elapsed_ms;           /* device time, including work redone after a rollback  */
+    int32_t proposal;            /* learned proposal: 0 none, 1 applied after this S,     */
+                                 /* 2 the previous proposal was rolled back and its      */
+                                 /* iteration redone without it before this one          */
+    int32_t reserved_;
 } agis_iter_stats;
 
 typedef struct agis_ctx agis_ctx;
@@ -224,6 +228,62 @@ int agis_abi_version(void);
 int agis_source_update_static(const agis_geometry* geo, const agis_config* cfg, const agis_obs* obs, int64_t n_obs,
                               double* src, int32_t n_src, const double* att, const double* cal, double* R_out,
                               double* W_out, double* stats_out, int32_t max_obs_per_source, void* stream);
+
+/* ---- Learned iteration proposal ---------------------------------------------------------
+ * Not part of the paper; its analogue there is the accelerated simple iteration (Sect. 4.7),
+ * which extrapolates the source updates with a factor estimated from successive updates.
+ * A network maps the last four updates of each source (and its observation count and
+ * ecliptic latitude) to a correction towards the converged solution:
+ *   features  22 per source: the last four updates d (oldest first; alpha* and delta as arcs,
+ *             rad and rad/yr) divided by their RMS sigma, log10(n_obs) - 2.5, sin(ecliptic
+ *             latitude)
+ *   network   22 -> 64 -> 64 -> 5, ReLU hidden layers; parameters as one FP32 vector in the
+ *             order W1[64][22], b1[64], W2[64][64], b2[64], W3[5][64], b3[5]
+ *   output    the correction sigma * y in the tangent units of d, added to the sources
+ * The forward runs on tensor cores with BF16 inputs, weights and hidden activations and
+ * FP32 accumulation; the training gradient is that of the same rounded forward. */
+#define AGIS_MLP_N_IN 22
+#define AGIS_MLP_N_HIDDEN 64
+#define AGIS_MLP_N_OUT 5
+#define AGIS_MLP_N_PARAMS 5957
+/* bytes of the packed (BF16, padded) weights that agis_mlp_pack writes */
+#define AGIS_MLP_PACKED_BYTES 16032
+
+/* Device-pointer kernels on `stream` (NULL: the legacy default stream); asynchronous.
+ * agis_mlp_pack        params (FP32, AGIS_MLP_N_PARAMS) -> packed weights for the forward
+ * agis_mlp_forward     X (n x 22 FP32, row-major) -> Y (n x 5 FP32)
+ * agis_mlp_loss_grad   loss = mean over the n rows of sum_j (y_j - t_j)^2 and its gradient
+ *                      with respect to params (grad: AGIS_MLP_N_PARAMS FP32, overwritten;
+ *                      loss: 1 FP32, overwritten); T: rows of 5; row r of the batch is row
+ *                      idx[r] of X and T (idx: n int32, device), or row r when idx is NULL
+ * agis_mlp_adam        one Adam step (Kingma & Ba 2015) with bias correction at step t >= 1;
+ *                      m, v: moment vectors (AGIS_MLP_N_PARAMS FP32, zero before step 1)
+ * agis_proposal_targets  T = (x_ref - x_k) / sigma in the tangent units of d, n x 5 FP32,
+ *                      from x_k, x_ref (n x 5 FP64) and sigma (n FP64)
+ * Errors: AGIS_E_INVALID (null pointer, n < 0, t < 1), AGIS_E_CUDA (launch failure). */
+int agis_mlp_pack(const float* params, void* packed, void* stream);
+int agis_mlp_forward(const void* packed, const float* X, int32_t n, float* Y, void* stream);
+int agis_mlp_loss_grad(const float* params, const float* X, const float* T, const int32_t* idx, int32_t n,
+                       float* grad, float* loss, void* stream);
+int agis_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t, float lr, float beta1, float beta2,
+                  float eps, void* stream);
+int agis_proposal_targets(const double* src_k, const double* src_ref, const double* sigma, int32_t n, float* T,
+                          void* stream);
+
+/* Enable the proposal in agis_iterate: params (host or device, AGIS_MLP_N_PARAMS FP32) are
+ * copied; every >= 5 is the number of iterations between proposals (the four updates the
+ * network sees are then plain ones).  After the S block of an iteration that qualifies, the
+ * proposal is added to the sources (and, to first order, to the residuals the A and C blocks
+ * read); the robust chi^2 of the next S block decides: if it is larger than before the
+ * proposal, the state before that iteration is restored and the iteration is redone without
+ * it.  params = NULL disables.  Errors: AGIS_E_INVALID, AGIS_E_OOM, AGIS_E_CUDA. */
+int agis_set_proposal(agis_ctx* ctx, const float* params, int32_t every);
+/* Features of the context's last four source updates and the current sources (device
+ * pointers: X n_src x 22 FP32, sigma n_src FP64), as the proposal uses them; a source with
+ * fewer than four updates since agis_init has zero history entries.  For training data. */
+int agis_get_proposal_features(agis_ctx* ctx, float* X, double* sigma);
+/* The current source parameters into a device array (n_src x 5 FP64, no host copy). */
+int agis_copy_sources_device(agis_ctx* ctx, double* src_dev);
 
 #ifdef __cplusplus
 }

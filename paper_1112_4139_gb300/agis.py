@@ -19,15 +19,18 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 2  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 3  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
     "agis_get_calibration", "agis_set_sources", "agis_set_attitude", "agis_set_calibration", "agis_get_residuals",
     "agis_get_source_stats", "agis_get_sizes", "agis_get_kernel_times", "agis_destroy", "agis_last_error",
-    "agis_abi_version", "agis_source_update_static",
+    "agis_abi_version", "agis_source_update_static", "agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad",
+    "agis_mlp_adam", "agis_proposal_targets", "agis_set_proposal", "agis_get_proposal_features",
+    "agis_copy_sources_device",
 )
 STATIC_MAX_OBS = 16384
+MLP_N_IN, MLP_N_OUT, MLP_N_PARAMS, MLP_PACKED_BYTES = 22, 5, 5957, 16032
 
 
 class Geometry(C.Structure):
@@ -69,7 +72,7 @@ class BlockStats(C.Structure):
 
 class IterStats(C.Structure):
     _fields_ = [("s", BlockStats), ("a", BlockStats), ("c", BlockStats), ("frame", C.c_double * 6),
-                ("elapsed_ms", C.c_double)]
+                ("elapsed_ms", C.c_double), ("proposal", C.c_int32), ("reserved_", C.c_int32)]
 
 
 _lib = None
@@ -115,6 +118,17 @@ def load():
         lib.agis_source_update_static.argtypes = [C.POINTER(Geometry), C.POINTER(Config), C.POINTER(Obs), C.c_int64,
                                                   P, C.c_int32, P, P, P, P, P, C.c_int32, P]
         lib.agis_source_update_static.restype = I
+        lib.agis_mlp_pack.argtypes = [P, P, V]
+        lib.agis_mlp_forward.argtypes = [P, P, C.c_int32, P, V]
+        lib.agis_mlp_loss_grad.argtypes = [P, P, P, P, C.c_int32, P, P, V]
+        lib.agis_mlp_adam.argtypes = [P, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, V]
+        lib.agis_proposal_targets.argtypes = [P, P, P, C.c_int32, P, V]
+        lib.agis_set_proposal.argtypes = [V, P, C.c_int32]
+        lib.agis_get_proposal_features.argtypes = [V, P, P]
+        lib.agis_copy_sources_device.argtypes = [V, P]
+        for f in ("agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad", "agis_mlp_adam", "agis_proposal_targets",
+                  "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device"):
+            getattr(lib, f).restype = I
         if lib.agis_abi_version() != ABI_VERSION:
             raise RuntimeError(f"libagis.so has ABI {lib.agis_abi_version()}, this binding {ABI_VERSION}: rebuild")
         _lib = lib
@@ -224,7 +238,7 @@ class Agis:
         done = C.c_int32(0)
         self._check(self._lib.agis_iterate(self.ctx, n_iter, C.cast(arr, C.c_void_p), C.byref(done)))
         return [dict(s=arr[k].s.as_dict(), a=arr[k].a.as_dict(), c=arr[k].c.as_dict(), frame=list(arr[k].frame),
-                     elapsed_ms=arr[k].elapsed_ms) for k in range(done.value)]
+                     elapsed_ms=arr[k].elapsed_ms, proposal=arr[k].proposal) for k in range(done.value)]
 
     # read-back
     def evaluate(self, out=None):
@@ -270,6 +284,59 @@ class Agis:
         ms = np.zeros(5)
         self._check(self._lib.agis_get_kernel_times(self.ctx, _ptr(ms)))
         return ms
+
+    # learned proposal
+    def set_proposal(self, params, every=5):
+        """Enable the proposal with FP32 parameters (host array or device tensor); None disables."""
+        if params is None:
+            self._check(self._lib.agis_set_proposal(self.ctx, None, 0))
+            return
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._lib.agis_set_proposal(self.ctx, _ptr(params), int(every)))
+
+    def proposal_features(self, X, sigma):
+        """Features (n_src x 22 FP32) and scales (n_src FP64) into device tensors."""
+        self._check(self._lib.agis_get_proposal_features(self.ctx, _ptr(X), _ptr(sigma)))
+
+    def copy_sources_device(self, out):
+        self._check(self._lib.agis_copy_sources_device(self.ctx, _ptr(out)))
+
+
+def _mlp_call(name, *args):
+    lib = load()
+    rc = getattr(lib, name)(*args)
+    if rc != AGIS_OK:
+        raise AgisError(rc, lib.agis_last_error(None).decode())
+
+
+def _stream(stream):
+    return C.c_void_p(stream) if stream is not None else None
+
+
+def mlp_pack(params, packed, stream=None):
+    """FP32 parameters (device) -> packed BF16 weights (device, MLP_PACKED_BYTES)."""
+    _mlp_call("agis_mlp_pack", _ptr(params), _ptr(packed), _stream(stream))
+
+
+def mlp_forward(packed, X, Y, stream=None):
+    _mlp_call("agis_mlp_forward", _ptr(packed), _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream))
+
+
+def mlp_loss_grad(params, X, T, grad, loss, idx=None, stream=None):
+    n = int(idx.shape[0]) if idx is not None else int(X.shape[0])
+    _mlp_call("agis_mlp_loss_grad", _ptr(params), _ptr(X), _ptr(T), _ptr(idx), n, _ptr(grad), _ptr(loss),
+              _stream(stream))
+
+
+def mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _mlp_call("agis_mlp_adam", _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr), float(beta1),
+              float(beta2), float(eps), _stream(stream))
+
+
+def proposal_targets(src_k, src_ref, sigma, T, stream=None):
+    _mlp_call("agis_proposal_targets", _ptr(src_k), _ptr(src_ref), _ptr(sigma), int(src_k.shape[0]), _ptr(T),
+              _stream(stream))
 
 
 def obs_from_dataset(ds, device=None):

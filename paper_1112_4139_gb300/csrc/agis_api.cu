@@ -40,6 +40,15 @@ void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const u
 void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
                     double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s);
 void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s);
+void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const double* corr, cudaStream_t s);
+void launch_hist_push(int32_t n_src, const double* d, double* hist, cudaStream_t s);
+void launch_prop_features(int32_t n_src, const double* hist, const int64_t* src_off, const double* src,
+                          double sin_obl, double cos_obl, float* X, double* sigma, cudaStream_t s);
+void launch_mlp_forward(const void* packed, const float* X, int n, float* Y, cudaStream_t s);
+void launch_prop_apply(int32_t n_src, const float* Y, const double* sigma, double* src, double* corr,
+                       cudaStream_t s);
+void launch_prop_rec(int32_t n_src, const int64_t* src_off, const double* scratch, ObsRec* rec, const double* corr,
+                     cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
                 double* dtil, int* rd, double* cal, cudaStream_t s);
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
@@ -237,10 +246,27 @@ struct agis_ctx {
     cudaEvent_t ev[kEvents];
     double ktimes[5] = {0, 0, 0, 0, 0};
     // per-block graphs: 0 S observation pass (FP64 model, or the mixed form's linearized
-    // correction), 1 A, 2 C, 3 frame, 4 mixed S pass with the full FP64 model, 5 S solves
-    static constexpr int kGraphs = 6;
-    cudaGraphExec_t graph_execs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graphs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // correction), 1 A, 2 C, 3 frame, 4 mixed S pass with the full FP64 model, 5 S solves,
+    // 6 learned proposal
+    static constexpr int kGraphs = 7;
+    cudaGraphExec_t graph_execs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graphs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // learned proposal: the last four source updates, the network, the state before the
+    // iteration that carries a proposal (for the rollback)
+    double* hist = nullptr;         // n_src x 4 x 5, oldest first
+    int hist_count = 0;             // source updates since agis_init / the last agis_set_*
+    void* prop_packed = nullptr;
+    float* prop_params = nullptr;
+    float* prop_X = nullptr;
+    float* prop_Y = nullptr;
+    double* prop_sigma = nullptr;
+    double* prop_corr = nullptr;
+    int prop_every = 0;
+    int since_prop = 1 << 30;
+    bool prop_pending = false;
+    double chi2_before_prop = 0.0;
+    double *snap_src = nullptr, *snap_att = nullptr, *snap_cal = nullptr, *snap_hist = nullptr;
+    int snap_hist_count = 0;
     bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
@@ -363,6 +389,19 @@ void enqueue_s_solve(agis_ctx* c) {
                             c->n_sblocks, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
+    launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
+}
+// learned proposal after the S block: features, network, sources += correction, and the
+// residuals that A and C read -= A correction
+void enqueue_proposal(agis_ctx* c) {
+    launch_prop_features(c->n_src, c->hist, c->src_off, c->src, c->G.sin_obl, c->G.cos_obl, c->prop_X,
+                         c->prop_sigma, c->stream);
+    launch_mlp_forward(c->prop_packed, c->prop_X, c->n_src, c->prop_Y, c->stream);
+    launch_prop_apply(c->n_src, c->prop_Y, c->prop_sigma, c->src, c->prop_corr, c->stream);
+    if (c->mixed)
+        launch_mix_prop(c->n_src, c->src_off, c->ms, c->prop_corr, c->stream);
+    else
+        launch_prop_rec(c->n_src, c->src_off, c->scratch, c->rec, c->prop_corr, c->stream);
 }
 void enqueue_a(agis_ctx* c) {
     if (c->mixed)
@@ -610,6 +649,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         (rc = dalloc(c, &c->sstats, 16)))
         return bail(rc);
     c->so.src = c->src;
+    if ((rc = dalloc(c, &c->hist, 20 * (size_t)n_src))) return bail(rc);
+    cudaMemsetAsync(c->hist, 0, sizeof(double) * 20 * (size_t)n_src, s);
     // ---- time order by knot interval
     c->n_iv = n_coef - 3;
     {
@@ -672,6 +713,7 @@ int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "source update");
     AGIS_CU(c, cudaGetLastError(), "source update kernels");
     s_done(c, refresh);
+    c->hist_count++;
     c->have_s = true;
     fill_s_stats(c, c->hstat, out);
     c->ktimes[0] = elapsed(c, 0, 1);
@@ -767,6 +809,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
     if (graph && !c->graphs_ready) {
         for (int b = 0; b < agis_ctx::kGraphs; b++) {
             if (b == 4 && !c->mixed) continue;
+            if (b == 6 && !c->prop_packed) continue;
             AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             if (b == 0) enqueue_s_pass(c, false);
             if (b == 4) enqueue_s_pass(c, true);
@@ -774,6 +817,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             if (b == 1) enqueue_a(c);
             if (b == 2) enqueue_c(c);
             if (b == 3 && c->ref) enqueue_frame(c, nullptr, c->n_src);
+            if (b == 6) enqueue_proposal(c);
             AGIS_CU(c, cudaStreamEndCapture(c->stream, &c->graphs[b]), "end capture");
             AGIS_CU(c, cudaGraphInstantiate(&c->graph_execs[b], c->graphs[b], 0), "instantiate graph");
         }
@@ -787,23 +831,84 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
         if (b == 1) enqueue_a(c);
         if (b == 2) enqueue_c(c);
         if (b == 3) enqueue_frame(c, nullptr, c->n_src);
+        if (b == 6) enqueue_proposal(c);
         return cuda_check(c, cudaGetLastError(), "block launch");
     };
-    for (int32_t k = 0; k < n_iter; k++) {
-        AGIS_CU(c, cudaEventRecord(c->ev[8], c->stream), "event");
-        const bool refresh = (mask & 1) && s_refresh_due(c);
-        if (mask & 1) AGIS_TRY(run_block(refresh ? 4 : 0));
+    const bool proposals = c->prop_every > 0 && (mask & 1);
+    auto snapshot = [&](bool save) -> int {
+        const size_t ns = 5 * (size_t)c->n_src, na = 4 * (size_t)c->n_coef, nc = (size_t)c->n_cal,
+                     nh = 20 * (size_t)c->n_src;
+        double *s0 = save ? c->snap_src : c->src, *s1 = save ? c->src : c->snap_src;
+        double *a0 = save ? c->snap_att : c->att, *a1 = save ? c->att : c->snap_att;
+        double *c0 = save ? c->snap_cal : c->cal, *c1 = save ? c->cal : c->snap_cal;
+        double *h0 = save ? c->snap_hist : c->hist, *h1 = save ? c->hist : c->snap_hist;
+        AGIS_CU(c, cudaMemcpyAsync(s0, s1, ns * 8, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+        AGIS_CU(c, cudaMemcpyAsync(a0, a1, na * 8, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+        AGIS_CU(c, cudaMemcpyAsync(c0, c1, nc * 8, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+        AGIS_CU(c, cudaMemcpyAsync(h0, h1, nh * 8, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+        if (save) {
+            c->snap_hist_count = c->hist_count;
+        } else {
+            c->hist_count = c->snap_hist_count;
+            c->mix_stale = true;   // the records describe the state that is being discarded
+        }
+        return AGIS_OK;
+    };
+    // one S block; returns its chi^2 (synchronises)
+    bool refresh = false;
+    auto run_s = [&](double& chi2) -> int {
+        refresh = s_refresh_due(c);
+        AGIS_TRY(run_block(refresh ? 4 : 0));
         AGIS_CU(c, cudaEventRecord(c->ev[12], c->stream), "event");
-        if (mask & 1) AGIS_TRY(run_block(5));
-        if (mask & 1) s_done(c, refresh);
+        AGIS_TRY(run_block(5));
+        s_done(c, refresh);
+        c->hist_count++;
+        AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                "stats");
+        AGIS_CU(c, cudaStreamSynchronize(c->stream), "source update");
+        chi2 = c->hstat[0];
+        return AGIS_OK;
+    };
+    auto run_acf = [&]() -> int {
+        if (mask & 2) AGIS_TRY(run_block(1));
+        if (mask & 4) AGIS_TRY(run_block(2));
+        if (do_frame) AGIS_TRY(run_block(3));
+        return AGIS_OK;
+    };
+    for (int32_t k = 0; k < n_iter; k++) {
+        int prop_state = 0;
+        const bool plan = proposals && !c->prop_pending && c->hist_count >= 3 && c->since_prop >= c->prop_every;
+        if (plan) AGIS_TRY(snapshot(true));
+        AGIS_CU(c, cudaEventRecord(c->ev[8], c->stream), "event");
+        double chi2 = 0.0;
+        if (mask & 1) AGIS_TRY(run_s(chi2));
+        if (c->prop_pending) {
+            c->prop_pending = false;
+            if (!(chi2 <= c->chi2_before_prop)) {
+                // the proposal did not lower the robust chi^2: back to the state before the
+                // iteration that carried it, which is redone without it, then this S again
+                AGIS_TRY(snapshot(false));
+                double chi2_redo = 0.0;
+                AGIS_TRY(run_s(chi2_redo));
+                AGIS_TRY(run_acf());
+                AGIS_TRY(run_s(chi2));
+                prop_state = 2;
+            }
+        }
+        if (plan && prop_state == 0) {
+            AGIS_TRY(run_block(6));
+            c->prop_pending = true;
+            c->chi2_before_prop = chi2;
+            c->since_prop = 0;
+            prop_state = 1;
+        }
         AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
         if (mask & 2) AGIS_TRY(run_block(1));
         AGIS_CU(c, cudaEventRecord(c->ev[10], c->stream), "event");
         if (mask & 4) AGIS_TRY(run_block(2));
         if (do_frame) AGIS_TRY(run_block(3));
         AGIS_CU(c, cudaEventRecord(c->ev[11], c->stream), "event");
-        AGIS_CU(c, cudaMemcpyAsync(c->hstat, c->sstats, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                "stats");
+        c->since_prop++;
         AGIS_CU(c, cudaMemcpyAsync(c->hisum, c->isum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream),
                 "stats");
         if (do_frame)
@@ -820,13 +925,14 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             if (do_frame)
                 for (int i = 0; i < 6; i++) it.frame[i] = c->hstat[16 + i];
             it.s.elapsed_ms = elapsed(c, 8, 9);
-            it.s.pass_ms = elapsed(c, 8, 12);
+            it.s.pass_ms = prop_state == 0 ? elapsed(c, 8, 12) : -1.0;
             it.s.full_eval = (mask & 1) && (!c->mixed || refresh) ? 1 : 0;
             it.a.elapsed_ms = elapsed(c, 9, 10);
             it.c.elapsed_ms = elapsed(c, 10, 11);
             it.elapsed_ms = elapsed(c, 8, 11);
+            it.proposal = prop_state;
         }
-        if ((mask & 1) && !std::isfinite(c->hstat[0])) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2");
+        if ((mask & 1) && !std::isfinite(chi2)) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2");
         if (n_done) *n_done = k + 1;
     }
     return AGIS_OK;
@@ -858,6 +964,10 @@ static int set_copy(agis_ctx* c, void* dst, const void* src, size_t bytes) {
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
     c->have_s = false;
     c->mix_stale = true;
+    c->hist_count = 0;
+    c->prop_pending = false;
+    AGIS_CU(c, cudaMemsetAsync(c->hist, 0, sizeof(double) * 20 * (size_t)c->n_src, c->stream), "history");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "history (sync)");
     return AGIS_OK;
 }
 int agis_set_sources(agis_ctx* c, const double* v) { return c ? set_copy(c, c->src, v, 5 * (size_t)c->n_src * 8) : AGIS_E_INVALID; }
@@ -889,6 +999,63 @@ int agis_get_source_stats(agis_ctx* c, double* stats_out, double* cov_out) {
         AGIS_TRY(get_copy(c, stats_out, buf, 5 * (size_t)c->n_src * 8));
     }
     if (cov_out) AGIS_TRY(get_copy(c, cov_out, c->so.cov, 25 * (size_t)c->n_src * 8));
+    return AGIS_OK;
+}
+
+int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
+    if (!c) return AGIS_E_INVALID;
+    if (!params) {
+        c->prop_every = 0;
+        c->prop_pending = false;
+        return AGIS_OK;
+    }
+    if (every < 5) return fail(c, AGIS_E_INVALID, "proposal period below 5 iterations");
+    if (!c->prop_packed) {
+        void* packed = nullptr;
+        AGIS_TRY(dalloc(c, reinterpret_cast<uint8_t**>(&packed), AGIS_MLP_PACKED_BYTES));
+        c->prop_packed = packed;
+        AGIS_TRY(dalloc(c, &c->prop_params, AGIS_MLP_N_PARAMS));
+        AGIS_TRY(dalloc(c, &c->prop_X, (size_t)AGIS_MLP_N_IN * c->n_src));
+        AGIS_TRY(dalloc(c, &c->prop_Y, (size_t)AGIS_MLP_N_OUT * c->n_src));
+        AGIS_TRY(dalloc(c, &c->prop_sigma, c->n_src));
+        AGIS_TRY(dalloc(c, &c->prop_corr, 5 * (size_t)c->n_src));
+        AGIS_TRY(dalloc(c, &c->snap_src, 5 * (size_t)c->n_src));
+        AGIS_TRY(dalloc(c, &c->snap_att, 4 * (size_t)c->n_coef));
+        AGIS_TRY(dalloc(c, &c->snap_cal, c->n_cal));
+        AGIS_TRY(dalloc(c, &c->snap_hist, 20 * (size_t)c->n_src));
+    }
+    AGIS_CU(c, cudaMemcpyAsync(c->prop_params, params, sizeof(float) * AGIS_MLP_N_PARAMS, cudaMemcpyDefault,
+                               c->stream),
+            "proposal parameters");
+    AGIS_TRY(agis_mlp_pack(c->prop_params, c->prop_packed, c->stream) == AGIS_OK
+                 ? AGIS_OK
+                 : fail(c, AGIS_E_CUDA, "packing the proposal network"));
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "proposal parameters (sync)");
+    c->prop_every = every;
+    c->prop_pending = false;
+    c->since_prop = 1 << 30;
+    // the per-block graphs are captured again with the proposal graph
+    for (int b = 0; b < agis_ctx::kGraphs; b++) {
+        if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
+        if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
+        c->graph_execs[b] = nullptr;
+        c->graphs[b] = nullptr;
+    }
+    c->graphs_ready = false;
+    return AGIS_OK;
+}
+
+int agis_get_proposal_features(agis_ctx* c, float* X, double* sigma) {
+    if (!c || !X || !sigma) return AGIS_E_INVALID;
+    launch_prop_features(c->n_src, c->hist, c->src_off, c->src, c->G.sin_obl, c->G.cos_obl, X, sigma, c->stream);
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "proposal features");
+    return cuda_check(c, cudaGetLastError(), "proposal features");
+}
+
+int agis_copy_sources_device(agis_ctx* c, double* dst) {
+    if (!c || !dst) return AGIS_E_INVALID;
+    AGIS_CU(c, cudaMemcpyAsync(dst, c->src, 5 * (size_t)c->n_src * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
     return AGIS_OK;
 }
 

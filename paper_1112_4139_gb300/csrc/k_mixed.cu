@@ -902,6 +902,27 @@ __global__ void k_mix_cal_project(int n_days, const double* __restrict__ dtil, d
     }
 }
 
+// R <- R - A c for a learned proposal c added to the sources (float-pair arithmetic)
+__global__ void k_mix_prop(int32_t n_src, const int64_t* __restrict__ src_off, MixS* __restrict__ ms,
+                           const double* __restrict__ corr) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_src; i += nw) {
+        float ch[5], cl[5];
+        for (int a = 0; a < 5; a++) split_pair(corr[5 * (size_t)i + a], ch[a], cl[a]);
+        for (int64_t o = src_off[i] + lane; o < src_off[i + 1]; o += kWarp) {
+            const MixS v = ms[o];
+            float A[5];
+            arow(v, A);
+            float sh, sl;
+            row_dot_pair(A, ch, cl, sh, sl);
+            float Rh = v.Rh, Rl = v.Rl;
+            pair_add(Rh, Rl, -sh, -sl);
+            *reinterpret_cast<float2*>(ms + o) = make_float2(Rh, Rl);
+        }
+    }
+}
+
 __global__ void k_mix_rw(int64_t n, const MixS* __restrict__ ms, double* __restrict__ R, double* __restrict__ W) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
         if (R) R[o] = (double)ms[o].Rh + (double)ms[o].Rl;
@@ -956,6 +977,10 @@ void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t
                     double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s) {
     k_mix_cal_accum<<<grid_of(n_cal, 8, 152 * 16), 256, 0, s>>>(n_cal, perm_c, cal_off, ms, dtil, rd);
     k_mix_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal, d_cal);
+}
+
+void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const double* corr, cudaStream_t s) {
+    k_mix_prop<<<grid_of(n_src, 8, 152 * 16), 256, 0, s>>>(n_src, src_off, ms, corr);
 }
 
 void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s) {
