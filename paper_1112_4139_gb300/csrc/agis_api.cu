@@ -16,9 +16,9 @@ void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
                      cudaStream_t stream);
-void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_order,
-                         int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch, int* work_counter,
-                         int n_blocks, cudaStream_t stream);
+void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
+                         const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
+                         int* work_counter, int n_blocks, cudaStream_t stream);
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
@@ -32,14 +32,14 @@ void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const u
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, MixS* ms, MixT* mt, double* geo, float* d_att,
                      float2* d_cal, int n_coef, int n_cal, cudaStream_t s);
-void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_order, int32_t n_src,
-                      const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s);
+void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_nal, const int32_t* src_order,
+                      int32_t n_src, const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s);
 void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
                           const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
                           double* blk, cudaStream_t s);
 void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
                     double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s);
-void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s);
+void launch_mix_rw(int64_t n, const uint32_t* perm, const MixS* ms, double* R, double* W, cudaStream_t s);
 void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const double* corr, cudaStream_t s);
 void launch_hist_push(int32_t n_src, const double* d, double* hist, cudaStream_t s);
 void launch_prop_features(int32_t n_src, const double* hist, const int64_t* src_off, const double* src,
@@ -91,10 +91,42 @@ __global__ void k_validate_pack(int64_t n, const int64_t* __restrict__ t, const 
     }
 }
 
-__global__ void k_copy_mu(int64_t n, const uint8_t* __restrict__ kind, const double* __restrict__ mu_in,
-                          double* __restrict__ mu) {
+// internal order: by source, AL before AC within a source (key 2 src + kind, stable sort)
+__global__ void k_class_keys(int64_t n, const int32_t* __restrict__ src, const uint8_t* __restrict__ kind,
+                             int32_t* __restrict__ key, uint32_t* __restrict__ val) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        key[o] = 2 * src[o] + (kind[o] ? 1 : 0);
+        val[o] = (uint32_t)o;
+    }
+}
+
+__global__ void k_gather_obs(int64_t n, const uint32_t* __restrict__ perm, const int64_t* __restrict__ t_in,
+                             const uint32_t* __restrict__ meta_in, const float* __restrict__ sig_in,
+                             const double* __restrict__ mu_in, const int32_t* __restrict__ src_in,
+                             int64_t* __restrict__ t, uint32_t* __restrict__ meta, float* __restrict__ sig,
+                             double* __restrict__ mu, int32_t* __restrict__ src) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = perm[o];
+        const uint32_t m = meta_in[p];
+        t[o] = t_in[p];
+        meta[o] = m;
+        sig[o] = sig_in[p];
+        mu[o] = meta_kind(m) ? mu_in[p] : 0.0;
+        src[o] = src_in[p];
+    }
+}
+
+// out[perm[o]] = in[o]: internal order back to the caller's order
+__global__ void k_scatter(int64_t n, const uint32_t* __restrict__ perm, const double* __restrict__ in,
+                          double* __restrict__ out) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
-        mu[o] = kind[o] ? mu_in[o] : 0.0;
+        out[perm[o]] = in[o];
+}
+
+// AL observations of each source from the offsets of the (source, kind) groups
+__global__ void k_src_nal(int32_t n_src, const int64_t* __restrict__ goff, int32_t* __restrict__ nal) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x)
+        nal[i] = (int32_t)(goff[2 * (size_t)i + 1] - goff[2 * (size_t)i]);
 }
 
 __global__ void k_check_finite(int64_t n, const double* __restrict__ v, int* __restrict__ err, int code) {
@@ -139,10 +171,11 @@ __global__ void k_src_counts(int32_t n_src, const int64_t* __restrict__ off, int
     }
 }
 
-__global__ void k_rec_rw(int64_t n, const ObsRec* __restrict__ rec, double* __restrict__ R, double* __restrict__ W) {
+__global__ void k_rec_rw(int64_t n, const uint32_t* __restrict__ perm, const ObsRec* __restrict__ rec,
+                         double* __restrict__ R, double* __restrict__ W) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        if (R) R[o] = rec[o].R;
-        if (W) W[o] = rec[o].W;
+        if (R) R[perm[o]] = rec[o].R;
+        if (W) W[perm[o]] = rec[o].W;
     }
 }
 
@@ -188,6 +221,8 @@ struct agis_ctx {
     float* sigma = nullptr;
     double* mu = nullptr;
     int32_t* obs_src = nullptr;
+    uint32_t* perm_in = nullptr;  // internal observation -> index in the caller's arrays
+    int32_t* src_nal = nullptr;   // AL observations of each source (they come first)
     int64_t* src_off = nullptr;
     int32_t* src_order = nullptr;
     // state
@@ -297,6 +332,23 @@ int dalloc(agis_ctx* c, T** p, size_t count) {
     return AGIS_OK;
 }
 
+// device temporary of the set-up, freed at the end of its scope
+struct TmpDev {
+    void* p = nullptr;
+    ~TmpDev() {
+        if (p) cudaFree(p);
+    }
+    template <typename T>
+    int alloc(agis_ctx* c, T** out, size_t count) {
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc (set-up)");
+        *out = (T*)p;
+        return AGIS_OK;
+    }
+};
+
 #define AGIS_TRY(x)                    \
     do {                               \
         int _r = (x);                  \
@@ -383,10 +435,10 @@ void enqueue_s_pass(agis_ctx* c, bool refresh) {
 }
 void enqueue_s_solve(agis_ctx* c) {
     if (c->mixed)
-        launch_mix_solve(c->st, c->src_off, c->src_order, c->n_src, c->so, c->ms, c->mw, c->stream);
+        launch_mix_solve(c->st, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->ms, c->mw, c->stream);
     else
-        launch_source_solve(c->st, c->meta, c->src_off, c->src_order, c->n_src, c->so, c->rec, c->scratch, c->work,
-                            c->n_sblocks, c->stream);
+        launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
+                            c->work, c->n_sblocks, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
@@ -548,37 +600,40 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         cudaMallocHost(&c->hisum, 4 * sizeof(long long)) != cudaSuccess)
         return bail(fail(c, AGIS_E_OOM, "pinned host buffer"));
     const int64_t n = n_obs;
-    // ---- observations
+    // ---- observations: copied in the caller's order, validated, then reordered
     int* derr = nullptr;
     int32_t* d_ccdrow = nullptr;
-    uint8_t *tmp8 = nullptr;
-    double* tmpmu = nullptr;
     int rc = AGIS_OK;
-    if ((rc = dalloc(c, &c->t_ns, n)) || (rc = dalloc(c, &c->meta, n)) || (rc = dalloc(c, &c->sigma, n)) ||
-        (rc = dalloc(c, &c->mu, n)) || (rc = dalloc(c, &c->obs_src, n)) || (rc = dalloc(c, &derr, 1)) ||
-        (rc = dalloc(c, &d_ccdrow, AGIS_N_CCD)) || (rc = dalloc(c, &tmp8, 3 * (size_t)n + 16)) ||
-        (rc = dalloc(c, &tmpmu, n)))
+    TmpDev tb_t, tb_src, tb_sig, tb_mu, tb_8, tb_meta;
+    int64_t* t_in = nullptr;
+    int32_t* src_in = nullptr;
+    float* sig_in = nullptr;
+    double* mu_in = nullptr;
+    uint8_t* tmp8 = nullptr;
+    uint32_t* meta_in = nullptr;
+    if ((rc = dalloc(c, &derr, 1)) || (rc = dalloc(c, &d_ccdrow, AGIS_N_CCD)) || (rc = tb_t.alloc(c, &t_in, n)) ||
+        (rc = tb_src.alloc(c, &src_in, n)) || (rc = tb_sig.alloc(c, &sig_in, n)) || (rc = tb_mu.alloc(c, &mu_in, n)) ||
+        (rc = tb_8.alloc(c, &tmp8, 3 * (size_t)n + 16)) || (rc = tb_meta.alloc(c, &meta_in, n)))
         return bail(rc);
     cudaStream_t s = c->stream;
 #define CP(dst, srcp, bytes)                                                                          \
     if (cuda_check(c, cudaMemcpyAsync((dst), (srcp), (bytes), cudaMemcpyDefault, s), "copy inputs")) \
         return bail(AGIS_E_CUDA);
     if (n > 0) {
-        CP(c->t_ns, obs->t_ns, n * sizeof(int64_t));
-        CP(c->obs_src, obs->src, n * sizeof(int32_t));
+        CP(t_in, obs->t_ns, n * sizeof(int64_t));
+        CP(src_in, obs->src, n * sizeof(int32_t));
         CP(tmp8, obs->ccd, n);
         CP(tmp8 + n, obs->fov, n);
         CP(tmp8 + 2 * n, obs->kind, n);
-        CP(c->sigma, obs->sigma, n * sizeof(float));
-        CP(tmpmu, obs->mu, n * sizeof(double));
+        CP(sig_in, obs->sigma, n * sizeof(float));
+        CP(mu_in, obs->mu, n * sizeof(double));
     }
     CP(d_ccdrow, geo->ccd_row, AGIS_N_CCD * sizeof(int32_t));
     cudaMemsetAsync(derr, 0, sizeof(int), s);
     if (n > 0) {
-        k_validate_pack<<<grid_for(n, 256), 256, 0, s>>>(n, c->t_ns, c->obs_src, tmp8, tmp8 + n, tmp8 + 2 * n,
-                                                         c->sigma, tmpmu, n_src, geo->cal_t0_ns, geo->cal_dt_ns,
-                                                         geo->n_cal_days, d_ccdrow, c->meta, derr);
-        k_copy_mu<<<grid_for(n, 256), 256, 0, s>>>(n, tmp8 + 2 * n, tmpmu, c->mu);
+        k_validate_pack<<<grid_for(n, 256), 256, 0, s>>>(n, t_in, src_in, tmp8, tmp8 + n, tmp8 + 2 * n, sig_in, mu_in,
+                                                         n_src, geo->cal_t0_ns, geo->cal_dt_ns, geo->n_cal_days,
+                                                         d_ccdrow, meta_in, derr);
     }
     // ---- state
     if ((rc = dalloc(c, &c->src, 5 * (size_t)n_src)) || (rc = dalloc(c, &c->att, 4 * (size_t)n_coef)) ||
@@ -606,6 +661,31 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
                       herr);
         return bail(fail(c, AGIS_E_INVALID, buf));
     }
+    // ---- internal order: by source, AL before AC (the per-class passes of the S block then
+    // sweep contiguous ranges)
+    if ((rc = dalloc(c, &c->t_ns, n)) || (rc = dalloc(c, &c->meta, n)) || (rc = dalloc(c, &c->sigma, n)) ||
+        (rc = dalloc(c, &c->mu, n)) || (rc = dalloc(c, &c->obs_src, n)) || (rc = dalloc(c, &c->perm_in, n)) ||
+        (rc = dalloc(c, &c->src_nal, n_src)))
+        return bail(rc);
+    {
+        TmpDev tk_in, tk_out, tv_in, tg;
+        int32_t *k_in = nullptr, *k_out = nullptr;
+        uint32_t* v_in = nullptr;
+        int64_t* goff = nullptr;
+        if ((rc = tk_in.alloc(c, &k_in, n)) || (rc = tk_out.alloc(c, &k_out, n)) || (rc = tv_in.alloc(c, &v_in, n)) ||
+            (rc = tg.alloc(c, &goff, 2 * (size_t)n_src + 1)))
+            return bail(rc);
+        if (n > 0) {
+            k_class_keys<<<grid_for(n, 256), 256, 0, s>>>(n, src_in, tmp8 + 2 * n, k_in, v_in);
+            if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_in, n, bits_for(2 * (int64_t)n_src)))) return bail(rc);
+            k_gather_obs<<<grid_for(n, 256), 256, 0, s>>>(n, c->perm_in, t_in, meta_in, sig_in, mu_in, src_in,
+                                                          c->t_ns, c->meta, c->sigma, c->mu, c->obs_src);
+        }
+        k_lower_bound<int32_t><<<grid_for(2 * (int64_t)n_src + 1, 256), 256, 0, s>>>(k_out, n,
+                                                                                      2 * (int64_t)n_src + 1, goff);
+        k_src_nal<<<grid_for(n_src, 256), 256, 0, s>>>(n_src, goff, c->src_nal);
+        if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
+    }
     // ---- source offsets, largest-first order, scratch capacity
     if ((rc = dalloc(c, &c->src_off, (size_t)n_src + 1)) || (rc = dalloc(c, &c->src_order, n_src))) return bail(rc);
     k_lower_bound<int32_t><<<grid_for(n_src + 1, 256), 256, 0, s>>>(c->obs_src, n, (int64_t)n_src + 1, c->src_off);
@@ -622,8 +702,10 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     }
     c->cap = (int)std::max<int64_t>(maxn, 32);
     {
+        TmpDev tk_in, tk_out, ti_in;
         int32_t *k_in = nullptr, *k_out = nullptr, *i_in = nullptr;
-        if ((rc = dalloc(c, &k_in, n_src)) || (rc = dalloc(c, &k_out, n_src)) || (rc = dalloc(c, &i_in, n_src)))
+        if ((rc = tk_in.alloc(c, &k_in, n_src)) || (rc = tk_out.alloc(c, &k_out, n_src)) ||
+            (rc = ti_in.alloc(c, &i_in, n_src)))
             return bail(rc);
         k_src_counts<<<grid_for(n_src, 256), 256, 0, s>>>(n_src, c->src_off, k_in, i_in);
         if (n_src > 0 && (rc = sort_pairs(c, k_in, k_out, (uint32_t*)i_in, (uint32_t*)c->src_order, n_src, 32)))
@@ -654,9 +736,10 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     // ---- time order by knot interval
     c->n_iv = n_coef - 3;
     {
+        TmpDev tk_in, tk_out, tv_in;
         int32_t *k_in = nullptr, *k_out = nullptr;
         uint32_t* v_in = nullptr;
-        if ((rc = dalloc(c, &k_in, n)) || (rc = dalloc(c, &k_out, n)) || (rc = dalloc(c, &v_in, n)) ||
+        if ((rc = tk_in.alloc(c, &k_in, n)) || (rc = tk_out.alloc(c, &k_out, n)) || (rc = tv_in.alloc(c, &v_in, n)) ||
             (rc = dalloc(c, &c->perm_t, n)) || (rc = dalloc(c, &c->ivl_off, (size_t)c->n_iv + 1)))
             return bail(rc);
         if (n > 0) {
@@ -671,6 +754,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
             if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_c, n, bits_for(n_cal)))) return bail(rc);
         }
         k_lower_bound<int32_t><<<grid_for(n_cal + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)n_cal + 1, c->cal_off);
+        if (cuda_check(c, cudaStreamSynchronize(s), "orders")) return bail(AGIS_E_CUDA);
     }
     // ---- segments and band storage
     {
@@ -941,8 +1025,10 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
 int agis_evaluate(agis_ctx* c, double* R_out) {
     if (!c || !R_out) return AGIS_E_INVALID;
     if (!c->evalR) AGIS_TRY(dalloc(c, &c->evalR, (size_t)c->n_obs));
+    if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
     launch_evaluate(c->G, c->t_ns, c->meta, c->mu, c->obs_src, c->n_obs, c->src, c->att, c->cal, c->evalR, c->stream);
-    AGIS_CU(c, cudaMemcpyAsync(R_out, c->evalR, c->n_obs * sizeof(double), cudaMemcpyDefault, c->stream), "copy R");
+    k_scatter<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->perm_in, c->evalR, c->tmpR);
+    AGIS_CU(c, cudaMemcpyAsync(R_out, c->tmpR, c->n_obs * sizeof(double), cudaMemcpyDefault, c->stream), "copy R");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "evaluate");
     return cuda_check(c, cudaGetLastError(), "evaluate kernels");
 }
@@ -980,9 +1066,9 @@ int agis_get_residuals(agis_ctx* c, double* R_out, double* W_out) {
     if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
     if (!c->tmpW) AGIS_TRY(dalloc(c, &c->tmpW, (size_t)c->n_obs));
     if (c->mixed)
-        launch_mix_rw(c->n_obs, c->ms, c->tmpR, c->tmpW, c->stream);
+        launch_mix_rw(c->n_obs, c->perm_in, c->ms, c->tmpR, c->tmpW, c->stream);
     else
-        k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->rec, c->tmpR, c->tmpW);
+        k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->perm_in, c->rec, c->tmpR, c->tmpW);
     if (R_out) AGIS_CU(c, cudaMemcpyAsync(R_out, c->tmpR, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy R");
     if (W_out) AGIS_CU(c, cudaMemcpyAsync(W_out, c->tmpW, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy W");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "residuals");

@@ -249,64 +249,52 @@ __device__ float mix_robust_sigma(const KeySrc& key, int n, int* hist, int lane)
 }
 
 // Class sums of one source for one round (whole warp), shifted to the previous solution:
-// h' = R - A dp, so that Q(y) = hh - 2 d'Ah + d'AA d is formed without cancellation.
-__device__ __forceinline__ void class_sums(const MixS* rs, int n, int lane, const SrcRound& in, int wfn,
+// h' = R - A dp, so that Q(y) = hh - 2 d'Ah + d'AA d is formed without cancellation.  The AL
+// rows of a source come first (rows [0, nal)), the AC rows after them.
+__device__ __forceinline__ void class_sums(const MixS* rs, int n, int nal, int lane, const SrcRound& in, int wfn,
                                            RoundSums* out) {
-    float AA[2][15], Ah[2][5], hh[2] = {0.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) AA[c][i] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 5; i++) Ah[c][i] = 0.0f;
-    }
-    int cnt = 0;
-    for (int j = lane; j < n; j += kWarp) {
-        const MixS r = rs[j];
-        float A[5];
-        arow(r, A);
-        const int cls = r.sig < 0.0f ? 1 : 0;
-        const float hp = r.Rh - adot(A, in.dp);
-        const float w = round_weight(in, r.Rh, hp, cls, wfn);
-        cnt += (w < 0.2f);
-        const float w1 = cls ? w : 0.0f, w0 = w - w1;
-#pragma unroll
-        for (int a = 0; a < 5; a++) {
-            const float wa0 = w0 * A[a], wa1 = w1 * A[a];
-#pragma unroll
-            for (int b = a; b < 5; b++) {
-                AA[0][up5(a, b)] = fmaf(wa0, A[b], AA[0][up5(a, b)]);
-                AA[1][up5(a, b)] = fmaf(wa1, A[b], AA[1][up5(a, b)]);
-            }
-            Ah[0][a] = fmaf(wa0, hp, Ah[0][a]);
-            Ah[1][a] = fmaf(wa1, hp, Ah[1][a]);
-        }
-        hh[0] = fmaf(w0 * hp, hp, hh[0]);
-        hh[1] = fmaf(w1 * hp, hp, hh[1]);
-    }
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) AA[c][i] = warp_sum_f(AA[c][i]);
-#pragma unroll
-        for (int i = 0; i < 5; i++) Ah[c][i] = warp_sum_f(Ah[c][i]);
-        hh[c] = warp_sum_f(hh[c]);
-    }
-    cnt = warp_sum_int(cnt);
-    // lanes write disjoint parts of the 176-byte record
     float* o = reinterpret_cast<float*>(out);
-#pragma unroll
+    int cnt = 0;
+#pragma unroll 1
     for (int c = 0; c < 2; c++) {
+        float AA[15], Ah[5], hh = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 15; i++) AA[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 5; i++) Ah[i] = 0.0f;
+        const int lo = c ? nal : 0, hi = c ? n : nal;
+        for (int j = lo + lane; j < hi; j += kWarp) {
+            const MixS r = rs[j];
+            float A[5];
+            arow(r, A);
+            const float hp = r.Rh - adot(A, in.dp);
+            const float w = round_weight(in, r.Rh, hp, c, wfn);
+            cnt += (w < 0.2f);
+#pragma unroll
+            for (int a = 0; a < 5; a++) {
+                const float wa = w * A[a];
+#pragma unroll
+                for (int b = a; b < 5; b++) AA[up5(a, b)] = fmaf(wa, A[b], AA[up5(a, b)]);
+                Ah[a] = fmaf(wa, hp, Ah[a]);
+            }
+            hh = fmaf(w * hp, hp, hh);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; i++) AA[i] = warp_sum_f(AA[i]);
+#pragma unroll
+        for (int i = 0; i < 5; i++) Ah[i] = warp_sum_f(Ah[i]);
+        hh = warp_sum_f(hh);
+        // lanes write disjoint parts of the 176-byte record
 #pragma unroll
         for (int i = 0; i < 15; i++)
-            if (lane == ((c * 15 + i) & 31)) o[c * 15 + i] = AA[c][i];
+            if (lane == i) o[c * 15 + i] = AA[i];
 #pragma unroll
         for (int i = 0; i < 5; i++)
-            if (lane == ((30 + c * 5 + i) & 31)) o[30 + c * 5 + i] = Ah[c][i];
+            if (lane == 15 + i) o[30 + c * 5 + i] = Ah[i];
+        if (lane == 20) o[40 + c] = hh;
     }
-    if (lane == 8) o[40] = hh[0];
-    if (lane == 9) o[41] = hh[1];
-    if (lane == 10) out->nout = cnt;
+    cnt = warp_sum_int(cnt);
+    if (lane == 21) out->nout = cnt;
 }
 
 // ---- general path (sigma varies within a class): per-observation sweeps for every
@@ -533,6 +521,7 @@ constexpr int kKeyCap = 1536;  // keys of a source kept in shared memory (6 KB p
 
 // sigma per class, robust scale and the round-0 class sums; one warp per source (largest first)
 __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st, const int64_t* __restrict__ src_off,
+                                                                     const int32_t* __restrict__ src_nal,
                                                                      const int32_t* __restrict__ src_order,
                                                                      int32_t n_src, const MixS* __restrict__ ms,
                                                                      MixSrcWork w) {
@@ -602,7 +591,7 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
             w.scale[i] = sc;
             w.round[i] = in;
         }
-        if (uni) class_sums(rs, n, lane, in, st.weight_fn, w.sums + i);
+        if (uni) class_sums(rs, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
         __syncwarp();
     }
 }
@@ -610,6 +599,7 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
 // class sums of round r >= 1 (weights and shift from the previous round's solution)
 constexpr int kSumWarps = 4;
 __global__ void __launch_bounds__(32 * kSumWarps) k_mix_sums(Settings st, const int64_t* __restrict__ src_off,
+                                                             const int32_t* __restrict__ src_nal,
                                                              const int32_t* __restrict__ src_order, int32_t n_src,
                                                              const MixS* __restrict__ ms, MixSrcWork w) {
     const int lane = threadIdx.x & 31;
@@ -620,7 +610,7 @@ __global__ void __launch_bounds__(32 * kSumWarps) k_mix_sums(Settings st, const 
         const int64_t o0 = src_off[i];
         const int n = (int)(src_off[i + 1] - o0);
         const SrcRound in = w.round[i];
-        class_sums(ms + o0, n, lane, in, st.weight_fn, w.sums + i);
+        class_sums(ms + o0, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
     }
 }
 
@@ -923,10 +913,11 @@ __global__ void k_mix_prop(int32_t n_src, const int64_t* __restrict__ src_off, M
     }
 }
 
-__global__ void k_mix_rw(int64_t n, const MixS* __restrict__ ms, double* __restrict__ R, double* __restrict__ W) {
+__global__ void k_mix_rw(int64_t n, const uint32_t* __restrict__ perm, const MixS* __restrict__ ms,
+                         double* __restrict__ R, double* __restrict__ W) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        if (R) R[o] = (double)ms[o].Rh + (double)ms[o].Rl;
-        if (W) W[o] = (double)ms[o].W;
+        if (R) R[perm[o]] = (double)ms[o].Rh + (double)ms[o].Rl;
+        if (W) W[perm[o]] = (double)ms[o].W;
     }
 }
 
@@ -951,15 +942,15 @@ void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const u
     cudaMemsetAsync(d_cal, 0, sizeof(float2) * (size_t)n_cal, s);
 }
 
-void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_order, int32_t n_src,
-                      const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s) {
+void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_nal, const int32_t* src_order,
+                      int32_t n_src, const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s) {
     const int rounds = st.robust ? st.n_rounds + 1 : 1;
     const int warp_blocks = grid_of(n_src, kSumWarps, 152 * 16);
     const int thread_blocks = (n_src + 127) / 128 > 0 ? (n_src + 127) / 128 : 1;
-    k_mix_scale_sums<<<grid_of(n_src, kScaleWarps, 152 * 8), 32 * kScaleWarps, 0, s>>>(st, src_off, src_order, n_src,
-                                                                                       ms, w);
+    k_mix_scale_sums<<<grid_of(n_src, kScaleWarps, 152 * 8), 32 * kScaleWarps, 0, s>>>(st, src_off, src_nal,
+                                                                                       src_order, n_src, ms, w);
     for (int r = 0; r < rounds; r++) {
-        if (r > 0) k_mix_sums<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_order, n_src, ms, w);
+        if (r > 0) k_mix_sums<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_nal, src_order, n_src, ms, w);
         k_mix_solve5<<<thread_blocks, 128, 0, s>>>(st, r == rounds - 1, src_off, n_src, out, w);
     }
     k_mix_final<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_order, n_src, out, ms, w);
@@ -983,8 +974,8 @@ void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const doub
     k_mix_prop<<<grid_of(n_src, 8, 152 * 16), 256, 0, s>>>(n_src, src_off, ms, corr);
 }
 
-void launch_mix_rw(int64_t n, const MixS* ms, double* R, double* W, cudaStream_t s) {
-    k_mix_rw<<<grid_of(n, 256, 152 * 32), 256, 0, s>>>(n, ms, R, W);
+void launch_mix_rw(int64_t n, const uint32_t* perm, const MixS* ms, double* R, double* W, cudaStream_t s) {
+    k_mix_rw<<<grid_of(n, 256, 152 * 32), 256, 0, s>>>(n, perm, ms, R, W);
 }
 
 }  // namespace agis

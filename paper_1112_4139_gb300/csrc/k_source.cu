@@ -152,11 +152,11 @@ __device__ __forceinline__ void pass_q(const double* scr, int n, int lane, const
     S2 = warp_sum(s);
 }
 
-// Sums of one class.  mode 0: w = wfun(x / vs) with x = h / sigma (initial downweighting);
-// mode 1: refresh w = wfun(R / sqrt(s2 + y_prev)) with R = h - A d_prev; mode 2: keep the stored
-// w.  The new w is stored in the scratch.  Each observation belongs to exactly one class, so
-// the two calls of a round visit every observation once.
-__device__ __forceinline__ void pass_class1(double* scr, int n, int lane, int cls, int mode, double vs, double sig,
+// Sums of one class over its contiguous range [lo, hi) of the source's rows (AL rows come
+// first).  mode 0: w = wfun(x / vs) with x = h / sigma (initial downweighting); mode 1:
+// refresh w = wfun(R / sqrt(s2 + y_prev)) with R = h - A d_prev; mode 2: keep the stored w.
+// The new w is stored in the scratch.
+__device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lane, int mode, double vs, double sig,
                                             const double* dp, double inv_sd, int wfn, double* AA, double* Ah,
                                             double& hh, int& nout) {
 #pragma unroll
@@ -165,9 +165,8 @@ __device__ __forceinline__ void pass_class1(double* scr, int n, int lane, int cl
     for (int i = 0; i < 5; i++) Ah[i] = 0.0;
     double hs = 0.0;
     int cnt = 0;
-    for (int j = lane; j < n; j += kWarp) {
+    for (int j = lo + lane; j < hi; j += kWarp) {
         double* e = scr + (size_t)j * kScr;
-        if ((e[7] != 0.0 ? 1 : 0) != cls) continue;
         const double h = e[0];
         const double A[5] = {e[1], e[2], e[3], e[4], e[5]};
         double w;
@@ -202,13 +201,13 @@ __device__ __forceinline__ void pass_class1(double* scr, int n, int lane, int cl
 
 // both classes; the sums (identical in every lane after the butterflies) go to the warp's
 // shared-memory slot so that they do not occupy registers during the 5x5 algebra
-__device__ __forceinline__ void pass_class(double* scr, int n, int lane, int mode, double vs, const double* sig_c,
-                                           const double* dp, const double* inv_sd, int wfn, ClassSums& S,
-                                           int& nout) {
+__device__ __forceinline__ void pass_class(double* scr, int n, int nal, int lane, int mode, double vs,
+                                           const double* sig_c, const double* dp, const double* inv_sd, int wfn,
+                                           ClassSums& S, int& nout) {
     int nc[2];
     for (int c = 0; c < 2; c++) {
         double AA[15], Ah[5], hh;
-        pass_class1(scr, n, lane, c, mode, vs, sig_c[c], dp, inv_sd[c], wfn, AA, Ah, hh, nc[c]);
+        pass_class1(scr, c ? nal : 0, c ? n : nal, lane, mode, vs, sig_c[c], dp, inv_sd[c], wfn, AA, Ah, hh, nc[c]);
         if (lane == 0) {
             for (int i = 0; i < 15; i++) S.AA[c][i] = AA[i];
             for (int i = 0; i < 5; i++) S.Ah[c][i] = Ah[i];
@@ -355,8 +354,8 @@ __device__ __noinline__ void solve_general(const Settings& st, int i, int64_t o0
 constexpr int kSolveWarps = 2;
 __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
     Settings st, const uint32_t* __restrict__ meta, const int64_t* __restrict__ src_off,
-    const int32_t* __restrict__ src_order, int32_t n_src, int batch, SrcOutPtrs out, ObsRec* __restrict__ rec,
-    double* __restrict__ scratch, int* work_counter) {
+    const int32_t* __restrict__ src_nal, const int32_t* __restrict__ src_order, int32_t n_src, int batch,
+    SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch, int* work_counter) {
     __shared__ int hist_all[kSolveWarps * 256];
     __shared__ ClassSums sums_all[kSolveWarps][kWarp];
     const int lane = threadIdx.x & 31;
@@ -375,6 +374,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
         const int my_i = mine ? src_order[base + lane] : 0;
         const int64_t my_o0 = mine ? src_off[my_i] : 0;
         const int my_n = mine ? (int)(src_off[my_i + 1] - my_o0) : 0;
+        const int my_nal = mine ? src_nal[my_i] : 0;
         double s5[5] = {0, 0, 0, 0, 0};
         if (mine)
             for (int k = 0; k < 5; k++) s5[k] = out.src[5 * (size_t)my_i + k];
@@ -414,9 +414,6 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                 vs = 0.5 * ((b0 + (h5 - lo5) * (b1 - b0)) - (a0 + (h1 - lo1) * (a1 - a0)));
                 __syncwarp();
             }
-            if (uni) {
-                for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 7] = (double)meta_kind(meta[o0 + j]);
-            }
             __syncwarp();
             if (lane == k) {
                 my_uniform = uni;
@@ -438,6 +435,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                 const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
                 if (n == 0 || !uni) continue;
                 const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+                const int nal = __shfl_sync(0xffffffffu, my_nal, k);
                 double dk[5];
                 for (int a = 0; a < 5; a++) dk[a] = __shfl_sync(0xffffffffu, d[a], k);
                 const double yk = __shfl_sync(0xffffffffu, y, k);
@@ -452,9 +450,9 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                         for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
                         __syncwarp();
                     }
-                    pass_class(scr, n, lane, 2, 0.0, sigc, dk, isd, st.weight_fn, sums[k], no);
+                    pass_class(scr, n, nal, lane, 2, 0.0, sigc, dk, isd, st.weight_fn, sums[k], no);
                 } else {
-                    pass_class(scr, n, lane, rnd == 0 ? 0 : 1, vsk, sigc, dk, isd, st.weight_fn, sums[k], no);
+                    pass_class(scr, n, nal, lane, rnd == 0 ? 0 : 1, vsk, sigc, dk, isd, st.weight_fn, sums[k], no);
                 }
                 if (lane == k) nout = no;
             }
@@ -483,6 +481,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
             const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
             if (n == 0 || !uni) continue;
             const int64_t o0 = __shfl_sync(0xffffffffu, my_o0, k);
+            const int nal = __shfl_sync(0xffffffffu, my_nal, k);
             double dk[5];
             for (int a = 0; a < 5; a++) dk[a] = __shfl_sync(0xffffffffu, d[a], k);
             const double yk = __shfl_sync(0xffffffffu, y, k);
@@ -493,7 +492,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
             for (int j = lane; j < n; j += kWarp) {
                 const double* e = scr + (size_t)j * kScr;
                 const double R = e[0] - (e[1] * dk[0] + e[2] * dk[1] + e[3] * dk[2] + e[4] * dk[3] + e[5] * dk[4]);
-                const double W = e[6] * iw[e[7] != 0.0 ? 1 : 0];
+                const double W = e[6] * (j < nal ? iw[0] : iw[1]);
                 ObsRec* r = rec + (o0 + j);
                 r->R = R;
                 r->W = W;
@@ -579,9 +578,9 @@ void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta,
 }
 
 // the per-source solves of the S block on the scratch rows of the observation pass
-void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_order,
-                         int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch, int* work_counter,
-                         int n_blocks, cudaStream_t stream) {
+void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
+                         const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
+                         int* work_counter, int n_blocks, cudaStream_t stream) {
     cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
     // batch size: 32 sources per warp when there are enough sources to keep ~16 warps per SM busy
     int batch = n_src / (152 * 16);
@@ -590,8 +589,8 @@ void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t
     int blocks = (warps + kSolveWarps - 1) / kSolveWarps;
     if (blocks > n_blocks * 4) blocks = n_blocks * 4;
     if (blocks < 1) blocks = 1;
-    k_source_solve<<<blocks, 32 * kSolveWarps, 0, stream>>>(st, meta, src_off, src_order, n_src, batch, out, rec,
-                                                            scratch, work_counter);
+    k_source_solve<<<blocks, 32 * kSolveWarps, 0, stream>>>(st, meta, src_off, src_nal, src_order, n_src, batch, out,
+                                                            rec, scratch, work_counter);
 }
 
 void launch_src_geo(int32_t n_src, const double* src, double* geo, cudaStream_t s) {
