@@ -42,6 +42,10 @@ FP64_PEAK_TFLOPS = 1.25
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per observation of the linearized observation pass (see time_form)
 MIX_PASS_BYTES = 8 + 16 + 4 + 8 + 8
+# DRAM bytes per observation (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
+# of 2.47e7 observations, scaled per observation; profiles/k_*_kernels_30k.md): the S block of
+# the FP64 form (observation pass + solves) and the mixed form's linearized pass
+TRAFFIC_PER_OBS = {"fp64_s_block": 866.0, "mixed_correct": 94.5}
 
 
 def parse():
@@ -461,7 +465,8 @@ def main():
         # is the FP64 unit count x clock (nominal 1.25 TFLOP/s on GB300)
         achieved = S_FLOPS_PER_OBS * ds.n_obs / (x["s_ms"] * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_obs_forward + k_source_solve (S block, FP64)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": TRAFFIC_PER_OBS["fp64_s_block"] * ds.n_obs,
                 "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock)", "flops_per_obs": S_FLOPS_PER_OBS}
 
     def mixed_roofline(x):
@@ -471,7 +476,8 @@ def main():
             return None
         achieved = MIX_PASS_BYTES * ds.n_obs / (x["pass_lin_ms"] * 1e-3) / 1e9
         return {"bound": "hbm", "kernel": "k_mix_correct (linearized observation pass)", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": TRAFFIC_PER_OBS["mixed_correct"] * ds.n_obs,
                 "peak_source": hbm_src, "bytes_per_obs": MIX_PASS_BYTES}
 
     def summary(name, x):

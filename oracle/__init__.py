@@ -17,6 +17,9 @@ Modules and the passages they follow:
             residuals, partial derivatives)
   blocks    Sects. 5.1-5.3 and 6.1 (S, A, C blocks and the frame rotator)
   agis      Sect. 4.6 (the S[ACG] simple iteration)
+  mlp       the learned iteration proposal (not in the paper; analogue of the
+            accelerated simple iteration of Sect. 4.7): network, loss, gradient,
+            Adam, features and targets
 
 Parity pins (tests/test_oracle_*.py) tie each part to the paper or to
 mathematics rather than to itself.  Every function without such a pin says so.
