@@ -100,20 +100,16 @@ __global__ void k_class_keys(int64_t n, const int32_t* __restrict__ src, const u
     }
 }
 
-__global__ void k_gather_obs(int64_t n, const uint32_t* __restrict__ perm, const int64_t* __restrict__ t_in,
-                             const uint32_t* __restrict__ meta_in, const float* __restrict__ sig_in,
-                             const double* __restrict__ mu_in, const int32_t* __restrict__ src_in,
-                             int64_t* __restrict__ t, uint32_t* __restrict__ meta, float* __restrict__ sig,
-                             double* __restrict__ mu, int32_t* __restrict__ src) {
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = perm[o];
-        const uint32_t m = meta_in[p];
-        t[o] = t_in[p];
-        meta[o] = m;
-        sig[o] = sig_in[p];
-        mu[o] = meta_kind(m) ? mu_in[p] : 0.0;
-        src[o] = src_in[p];
-    }
+// out[o] = in[perm[o]]: the caller's order to the internal order, one array at a time
+template <typename T>
+__global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ in, T* __restrict__ out) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+        out[o] = in[perm[o]];
+}
+__global__ void k_gather_mu(int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ meta,
+                            const double* __restrict__ in, double* __restrict__ out) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+        out[o] = meta_kind(meta[o]) ? in[perm[o]] : 0.0;
 }
 
 // out[perm[o]] = in[o]: internal order back to the caller's order
@@ -335,8 +331,10 @@ int dalloc(agis_ctx* c, T** p, size_t count) {
 // device temporary of the set-up, freed at the end of its scope
 struct TmpDev {
     void* p = nullptr;
-    ~TmpDev() {
+    ~TmpDev() { release(); }
+    void release() {
         if (p) cudaFree(p);
+        p = nullptr;
     }
     template <typename T>
     int alloc(agis_ctx* c, T** out, size_t count) {
@@ -663,10 +661,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     }
     // ---- internal order: by source, AL before AC (the per-class passes of the S block then
     // sweep contiguous ranges)
-    if ((rc = dalloc(c, &c->t_ns, n)) || (rc = dalloc(c, &c->meta, n)) || (rc = dalloc(c, &c->sigma, n)) ||
-        (rc = dalloc(c, &c->mu, n)) || (rc = dalloc(c, &c->obs_src, n)) || (rc = dalloc(c, &c->perm_in, n)) ||
-        (rc = dalloc(c, &c->src_nal, n_src)))
-        return bail(rc);
+    // (each array is gathered into its internal copy and its caller-order copy released
+    // before the next, which keeps the set-up's peak memory near 60 bytes per observation)
+    if ((rc = dalloc(c, &c->perm_in, n)) || (rc = dalloc(c, &c->src_nal, n_src))) return bail(rc);
     {
         TmpDev tk_in, tk_out, tv_in, tg;
         int32_t *k_in = nullptr, *k_out = nullptr;
@@ -678,14 +675,32 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         if (n > 0) {
             k_class_keys<<<grid_for(n, 256), 256, 0, s>>>(n, src_in, tmp8 + 2 * n, k_in, v_in);
             if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_in, n, bits_for(2 * (int64_t)n_src)))) return bail(rc);
-            k_gather_obs<<<grid_for(n, 256), 256, 0, s>>>(n, c->perm_in, t_in, meta_in, sig_in, mu_in, src_in,
-                                                          c->t_ns, c->meta, c->sigma, c->mu, c->obs_src);
         }
         k_lower_bound<int32_t><<<grid_for(2 * (int64_t)n_src + 1, 256), 256, 0, s>>>(k_out, n,
                                                                                       2 * (int64_t)n_src + 1, goff);
         k_src_nal<<<grid_for(n_src, 256), 256, 0, s>>>(n_src, goff, c->src_nal);
         if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
     }
+    tb_8.release();
+    const uint32_t* pin = c->perm_in;
+    if ((rc = dalloc(c, &c->t_ns, n))) return bail(rc);
+    k_gather<int64_t><<<grid_for(n, 256), 256, 0, s>>>(n, pin, t_in, c->t_ns);
+    if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
+    tb_t.release();
+    if ((rc = dalloc(c, &c->meta, n))) return bail(rc);
+    k_gather<uint32_t><<<grid_for(n, 256), 256, 0, s>>>(n, pin, meta_in, c->meta);
+    if ((rc = dalloc(c, &c->mu, n))) return bail(rc);
+    k_gather_mu<<<grid_for(n, 256), 256, 0, s>>>(n, pin, c->meta, mu_in, c->mu);
+    if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
+    tb_mu.release();
+    tb_meta.release();
+    if ((rc = dalloc(c, &c->sigma, n))) return bail(rc);
+    k_gather<float><<<grid_for(n, 256), 256, 0, s>>>(n, pin, sig_in, c->sigma);
+    if ((rc = dalloc(c, &c->obs_src, n))) return bail(rc);
+    k_gather<int32_t><<<grid_for(n, 256), 256, 0, s>>>(n, pin, src_in, c->obs_src);
+    if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
+    tb_sig.release();
+    tb_src.release();
     // ---- source offsets, largest-first order, scratch capacity
     if ((rc = dalloc(c, &c->src_off, (size_t)n_src + 1)) || (rc = dalloc(c, &c->src_order, n_src))) return bail(rc);
     k_lower_bound<int32_t><<<grid_for(n_src + 1, 256), 256, 0, s>>>(c->obs_src, n, (int64_t)n_src + 1, c->src_off);
@@ -711,28 +726,6 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         if (n_src > 0 && (rc = sort_pairs(c, k_in, k_out, (uint32_t*)i_in, (uint32_t*)c->src_order, n_src, 32)))
             return bail(rc);
     }
-    c->n_sblocks = c->n_sm * 8;
-    c->mixed = cfg->precision == 1;
-    if (c->mixed) {
-        if ((rc = dalloc(c, &c->ms, n)) || (rc = dalloc(c, &c->mt, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
-            (rc = dalloc(c, &c->d_cal, n_cal)) || (rc = dalloc(c, &c->mw.scale, n_src)) ||
-            (rc = dalloc(c, &c->mw.round, n_src)) || (rc = dalloc(c, &c->mw.fin, n_src)) ||
-            (rc = dalloc(c, &c->mw.sums, n_src)))
-            return bail(rc);
-    } else {
-        if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
-    }
-    if ((rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
-        (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
-        (rc = dalloc(c, &c->so.eps2, n_src)) || (rc = dalloc(c, &c->so.q, n_src)) ||
-        (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||
-        (rc = dalloc(c, &c->so.cov, 25 * (size_t)n_src)) || (rc = dalloc(c, &c->so.nu, n_src)) ||
-        (rc = dalloc(c, &c->so.nout, n_src)) || (rc = dalloc(c, &c->so.rankdef, n_src)) ||
-        (rc = dalloc(c, &c->sstats, 16)))
-        return bail(rc);
-    c->so.src = c->src;
-    if ((rc = dalloc(c, &c->hist, 20 * (size_t)n_src))) return bail(rc);
-    cudaMemsetAsync(c->hist, 0, sizeof(double) * 20 * (size_t)n_src, s);
     // ---- time order by knot interval
     c->n_iv = n_coef - 3;
     {
@@ -756,6 +749,28 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         k_lower_bound<int32_t><<<grid_for(n_cal + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)n_cal + 1, c->cal_off);
         if (cuda_check(c, cudaStreamSynchronize(s), "orders")) return bail(AGIS_E_CUDA);
     }
+    c->n_sblocks = c->n_sm * 8;
+    c->mixed = cfg->precision == 1;
+    if (c->mixed) {
+        if ((rc = dalloc(c, &c->ms, n)) || (rc = dalloc(c, &c->mt, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
+            (rc = dalloc(c, &c->d_cal, n_cal)) || (rc = dalloc(c, &c->mw.scale, n_src)) ||
+            (rc = dalloc(c, &c->mw.round, n_src)) || (rc = dalloc(c, &c->mw.fin, n_src)) ||
+            (rc = dalloc(c, &c->mw.sums, n_src)))
+            return bail(rc);
+    } else {
+        if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
+    }
+    if ((rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
+        (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
+        (rc = dalloc(c, &c->so.eps2, n_src)) || (rc = dalloc(c, &c->so.q, n_src)) ||
+        (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||
+        (rc = dalloc(c, &c->so.cov, 25 * (size_t)n_src)) || (rc = dalloc(c, &c->so.nu, n_src)) ||
+        (rc = dalloc(c, &c->so.nout, n_src)) || (rc = dalloc(c, &c->so.rankdef, n_src)) ||
+        (rc = dalloc(c, &c->sstats, 16)))
+        return bail(rc);
+    c->so.src = c->src;
+    if ((rc = dalloc(c, &c->hist, 20 * (size_t)n_src))) return bail(rc);
+    cudaMemsetAsync(c->hist, 0, sizeof(double) * 20 * (size_t)n_src, s);
     // ---- segments and band storage
     {
         std::vector<int32_t> sl, sn, su;
