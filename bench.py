@@ -72,6 +72,10 @@ def parse():
                     help="convergence: also the mixed form with the learned proposal, trained first on two "
                          "held-out 100k-source 5-year sets")
     ap.add_argument("--proposal-every", type=int, default=5, help="iterations between learned proposals")
+    ap.add_argument("--asi", action="store_true",
+                    help="with --convergence: also the accelerated simple iteration (Sect. 4.7) in both forms")
+    ap.add_argument("--asi-stride", type=int, default=16, help="ASI: every n-th source enters the lambda estimate")
+    ap.add_argument("--asi-lambda-max", type=float, default=0.9, help="ASI: clamp of the lambda estimate")
     return ap.parse_args()
 
 
@@ -335,16 +339,18 @@ def run_convergence(args, agis, ds, stream, rank):
         return j + 1, float(np.sum(times[:j + 1])) * 1e-3
 
     it64, s64 = first_below(rms64, t64)
-    # mixed form against the same reference
-    def run_mixed(params=None, extra=3):
-        g = open_form(1)
+    # the other runs against the same reference
+    def run_mixed(params=None, extra=3, asi=False, prec=1):
+        g = open_form(prec)
         if params is not None:
             g.set_proposal(params, args.proposal_every)
+        if asi:
+            g.set_asi(args.asi_stride, args.asi_lambda_max)
         rms, tms, props, per_param, below = [], [], [], None, 0
         for k in range(args.ref_max_iter):
             its = g.iterate(1)
             tms.append(its[0]["elapsed_ms"])
-            props.append(its[0]["proposal"])
+            props.append(its[0]["asi_factor"] if asi else its[0]["proposal"])
             e = diff_uas(g.sources(), x_ref)
             rms.append(float(np.sqrt(np.mean(e ** 2))))
             below = below + 1 if rms[-1] <= 1.0 else 0
@@ -386,6 +392,16 @@ def run_convergence(args, agis, ds, stream, rank):
                                      "seconds": round(t_train, 1)},
                         "speedup_vs_mixed": (sm / sl) if (sm and sl) else None,
                         "iterations_saved_vs_mixed": (itm - itl) if (itm and itl) else None}
+    asi_lines = {}
+    if args.asi:
+        # the paper's own accelerator (Sect. 4.7) in both forms
+        for name, prec in (("mixed_asi", 1), ("fp64_asi", 0)):
+            rmsa, ta, fac, per_a = run_mixed(asi=True, prec=prec)
+            ita, sa = first_below(rmsa, ta)
+            asi_lines[name] = {"iterations": ita, "seconds": sa, "ms_per_iter": float(np.median(ta)),
+                               "stride": args.asi_stride, "lambda_max": args.asi_lambda_max,
+                               "factors": [round(v, 3) for v in fac], "rms_uas": [round(v, 4) for v in rmsa],
+                               "per_param_rms_uas_at_1uas": per_a}
     line = {"metric": "wall time to 1 uas RMS vs FP64 reference", "unit": "s", "higher_is_better": False,
             "workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs, "n_src": ds.n_src,
             "reference": {"form": "fp64", "iterations": len(rms64), "last_max_update_uas": ref_last_update,
@@ -396,6 +412,11 @@ def run_convergence(args, agis, ds, stream, rank):
                       "refresh_every": args.refresh_every, "rms_uas": [round(v, 4) for v in rmsm],
                       "per_param_rms_uas_at_1uas": per_param},
             "speedup": (s64 / sm) if (s64 and sm) else None}
+    line.update(asi_lines)
+    if "fp64_asi" in asi_lines and s64 and asi_lines["fp64_asi"]["seconds"]:
+        line["speedup_fp64_asi_vs_fp64"] = s64 / asi_lines["fp64_asi"]["seconds"]
+    if "mixed_asi" in asi_lines and s64 and asi_lines["mixed_asi"]["seconds"]:
+        line["speedup_mixed_asi_vs_fp64"] = s64 / asi_lines["mixed_asi"]["seconds"]
     if learned_line is not None:
         line["mixed_learned"] = learned_line
         line["speedup_learned_vs_fp64"] = (s64 / learned_line["seconds"]) if (s64 and learned_line["seconds"]) else None

@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 3
+#define AGIS_ABI_VERSION 4
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -124,7 +124,9 @@ typedef struct agis_iter_stats {
     int32_t proposal;            /* learned proposal: 0 none, 1 applied after this S,     */
                                  /* 2 the previous proposal was rolled back and its      */
                                  /* iteration redone without it before this one          */
-    int32_t reserved_;
+    int32_t asi_n;               /* ASI: sample ratios the estimate used (0: not applied) */
+    double asi_lambda;           /* ASI: median ratio of successive parallax updates     */
+    double asi_factor;           /* ASI: factor 1/(1 - lambda) applied (1: none)         */
 } agis_iter_stats;
 
 typedef struct agis_ctx agis_ctx;
@@ -284,6 +286,39 @@ int agis_set_proposal(agis_ctx* ctx, const float* params, int32_t every);
 int agis_get_proposal_features(agis_ctx* ctx, float* X, double* sigma);
 /* The current source parameters into a device array (n_src x 5 FP64, no host copy). */
 int agis_copy_sources_device(agis_ctx* ctx, double* src_dev);
+
+/* ---------------------------------------------------------------------------------------
+ * Accelerated simple iteration (ASI, Sect. 4.7)
+ *
+ * Once the updates of successive iterations are nearly proportional, d^(k+1) ~ lambda d^(k),
+ * the updates still to come sum to d^(k+1) / (1 - lambda) (a geometric series), and ASI
+ * applies that factor to the update of the iteration.  In agis_iterate, after the S block
+ * of every iteration that has the source updates of two S blocks behind it:
+ *   r_i     = d_varpi,i^(k+1) / d_varpi,i^(k) for the sample sources i = 0, m, 2m, ...
+ *             (m = stride; parallax updates, which a change of the frame orientation
+ *             leaves alone); sources with a zero or non-finite ratio are skipped
+ *   lambda  = the lower median of the r_i, clamped to [0, lambda_max]
+ *   sources += (1/(1 - lambda) - 1) d^(k+1), alpha* turned into alpha with cos(delta),
+ *             and the residuals the A and C blocks read -= A times that correction
+ *             (first order), so that A and C solve against the extrapolated sources.
+ * The factor multiplies the source update only: for two coupled blocks iterated in
+ * Gauss-Seidel order the error component along the slowest eigenvector vanishes when the
+ * update of one block is extrapolated with its exact lambda, and overshoots when both are.
+ * The ratios are those of the plain S-block updates, before extrapolation.  An iteration
+ * that carries a learned proposal is not also extrapolated.
+ * stride <= 0 disables; lambda_max in [0, 1).  Errors: AGIS_E_INVALID, AGIS_E_OOM,
+ * AGIS_E_CUDA. */
+int agis_set_asi(agis_ctx* ctx, int32_t stride, double lambda_max);
+/* The ASI estimate on its own, from two source updates in device memory (d_prev, d_cur:
+ * n_src x 5 FP64, parallax at column 2): est[0] the lower median of the ratios
+ * d_cur/d_prev over the sources i = 0, stride, 2 stride, ... with d_prev != 0 and a finite
+ * ratio, est[1] that median clamped to [0, lambda_max], est[2] = 1/(1 - est[1]), est[3] the
+ * number of ratios (all zero but est[2] = 1 when there are none).  est: 4 FP64 on the device;
+ * scratch: ceil(n_src / stride) x 8 bytes on the device.  Asynchronous on `stream`.
+ * Errors: AGIS_E_INVALID (null pointer, n_src < 1, stride < 1, lambda_max outside [0, 1)),
+ * AGIS_E_CUDA. */
+int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, int32_t stride, double lambda_max,
+                      void* scratch, double* est, void* stream);
 
 #ifdef __cplusplus
 }

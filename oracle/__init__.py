@@ -17,6 +17,7 @@ Modules and the passages they follow:
             residuals, partial derivatives)
   blocks    Sects. 5.1-5.3 and 6.1 (S, A, C blocks and the frame rotator)
   agis      Sect. 4.6 (the S[ACG] simple iteration)
+  asi       Sect. 4.7 (the accelerated simple iteration)
   mlp       the learned iteration proposal (not in the paper; analogue of the
             accelerated simple iteration of Sect. 4.7): network, loss, gradient,
             Adam, features and targets

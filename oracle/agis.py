@@ -30,16 +30,21 @@ class IterStats:
     d_rms: np.ndarray      # RMS of the 5 source updates (rad, rad/yr)
 
 
-def iterate_once(P, state, st, ref=None):
+def iterate_once(P, state, st, ref=None, after_s=None):
     """One AGIS iteration in the order of Sect. 4.6: s^(k+1) from a^(k), c^(k); then a^(k+1)
-    and c^(k+1) both from s^(k+1) with the old a^(k), c^(k); then the frame rotator."""
+    and c^(k+1) both from s^(k+1) with the old a^(k), c^(k); then the frame rotator.
+    after_s(src1, sres, ev) -> (src1, R), if given, changes the sources after the S block and
+    returns the residuals the A and C blocks read (the accelerated iteration, Sect. 4.7)."""
     src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st)
+    R = sres.R
+    if after_s is not None:
+        src1, R = after_s(src1, sres, ev)
     att1, rda = state.att.copy(), 0
     cal1, rdc = state.cal.copy(), 0
     if "A" in st.block_mask:
-        att1, rda = B.attitude_update(P, state.att, ev, sres.R, sres.W, st)
+        att1, rda = B.attitude_update(P, state.att, ev, R, sres.W, st)
     if "C" in st.block_mask:
-        cal1, rdc = B.calibration_update(P, state.cal, ev, sres.R, sres.W)
+        cal1, rdc = B.calibration_update(P, state.cal, ev, R, sres.W)
     frame = np.zeros(6)
     if st.frame_each_iter and ref is not None:
         eps, om = B.frame_fit(P, src1, ref)

@@ -19,7 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 3  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 4  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -27,7 +27,7 @@ EXPORTS = (
     "agis_get_source_stats", "agis_get_sizes", "agis_get_kernel_times", "agis_destroy", "agis_last_error",
     "agis_abi_version", "agis_source_update_static", "agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad",
     "agis_mlp_adam", "agis_proposal_targets", "agis_set_proposal", "agis_get_proposal_features",
-    "agis_copy_sources_device",
+    "agis_copy_sources_device", "agis_set_asi", "agis_asi_estimate",
 )
 STATIC_MAX_OBS = 16384
 MLP_N_IN, MLP_N_OUT, MLP_N_PARAMS, MLP_PACKED_BYTES = 22, 5, 5957, 16032
@@ -72,7 +72,8 @@ class BlockStats(C.Structure):
 
 class IterStats(C.Structure):
     _fields_ = [("s", BlockStats), ("a", BlockStats), ("c", BlockStats), ("frame", C.c_double * 6),
-                ("elapsed_ms", C.c_double), ("proposal", C.c_int32), ("reserved_", C.c_int32)]
+                ("elapsed_ms", C.c_double), ("proposal", C.c_int32), ("asi_n", C.c_int32),
+                ("asi_lambda", C.c_double), ("asi_factor", C.c_double)]
 
 
 _lib = None
@@ -126,8 +127,11 @@ def load():
         lib.agis_set_proposal.argtypes = [V, P, C.c_int32]
         lib.agis_get_proposal_features.argtypes = [V, P, P]
         lib.agis_copy_sources_device.argtypes = [V, P]
+        lib.agis_set_asi.argtypes = [V, C.c_int32, C.c_double]
+        lib.agis_asi_estimate.argtypes = [P, P, C.c_int32, C.c_int32, C.c_double, P, P, V]
         for f in ("agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad", "agis_mlp_adam", "agis_proposal_targets",
-                  "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device"):
+                  "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device", "agis_set_asi",
+                  "agis_asi_estimate"):
             getattr(lib, f).restype = I
         if lib.agis_abi_version() != ABI_VERSION:
             raise RuntimeError(f"libagis.so has ABI {lib.agis_abi_version()}, this binding {ABI_VERSION}: rebuild")
@@ -238,7 +242,8 @@ class Agis:
         done = C.c_int32(0)
         self._check(self._lib.agis_iterate(self.ctx, n_iter, C.cast(arr, C.c_void_p), C.byref(done)))
         return [dict(s=arr[k].s.as_dict(), a=arr[k].a.as_dict(), c=arr[k].c.as_dict(), frame=list(arr[k].frame),
-                     elapsed_ms=arr[k].elapsed_ms, proposal=arr[k].proposal) for k in range(done.value)]
+                     elapsed_ms=arr[k].elapsed_ms, proposal=arr[k].proposal, asi_n=arr[k].asi_n,
+                     asi_lambda=arr[k].asi_lambda, asi_factor=arr[k].asi_factor) for k in range(done.value)]
 
     # read-back
     def evaluate(self, out=None):
@@ -302,6 +307,12 @@ class Agis:
     def copy_sources_device(self, out):
         self._check(self._lib.agis_copy_sources_device(self.ctx, _ptr(out)))
 
+    # accelerated simple iteration
+    def set_asi(self, stride=16, lambda_max=0.9):
+        """Extrapolate the source update of each iteration by 1/(1 - lambda), lambda from the
+        parallax updates of every stride-th source; stride 0 disables."""
+        self._check(self._lib.agis_set_asi(self.ctx, int(stride), float(lambda_max)))
+
 
 def _mlp_call(name, *args):
     lib = load()
@@ -337,6 +348,13 @@ def mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream
 def proposal_targets(src_k, src_ref, sigma, T, stream=None):
     _mlp_call("agis_proposal_targets", _ptr(src_k), _ptr(src_ref), _ptr(sigma), int(src_k.shape[0]), _ptr(T),
               _stream(stream))
+
+
+def asi_estimate(d_prev, d_cur, stride, lambda_max, scratch, est, stream=None):
+    """ASI estimate [median, lambda, factor, count] into est (4 FP64, device) from two
+    n_src x 5 FP64 device updates; scratch: ceil(n_src / stride) x 8 bytes on the device."""
+    _mlp_call("agis_asi_estimate", _ptr(d_prev), _ptr(d_cur), int(d_cur.shape[0]), int(stride), float(lambda_max),
+              _ptr(scratch), _ptr(est), _stream(stream))
 
 
 def obs_from_dataset(ds, device=None):

@@ -49,6 +49,8 @@ void launch_prop_apply(int32_t n_src, const float* Y, const double* sigma, doubl
                        cudaStream_t s);
 void launch_prop_rec(int32_t n_src, const int64_t* src_off, const double* scratch, ObsRec* rec, const double* corr,
                      cudaStream_t s);
+void launch_asi(int32_t n_src, int32_t stride, const double* hist, double lam_max, unsigned long long* keys,
+                double* est, const double* d, double* src, double* corr, cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
                 double* dtil, int* rd, double* cal, cudaStream_t s);
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
@@ -270,7 +272,7 @@ struct agis_ctx {
     double* tmpR = nullptr;
     double* tmpW = nullptr;
     // host read-back (pinned)
-    double* hstat = nullptr;      // 10 S + 6 frame
+    double* hstat = nullptr;      // 10 S, 6 frame at 16, 4 ASI estimate at 24
     long long* hisum = nullptr;   // 2
     bool have_s = false;
     static constexpr int kEvents = 14;
@@ -278,10 +280,10 @@ struct agis_ctx {
     double ktimes[5] = {0, 0, 0, 0, 0};
     // per-block graphs: 0 S observation pass (FP64 model, or the mixed form's linearized
     // correction), 1 A, 2 C, 3 frame, 4 mixed S pass with the full FP64 model, 5 S solves,
-    // 6 learned proposal
-    static constexpr int kGraphs = 7;
-    cudaGraphExec_t graph_execs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graphs[kGraphs] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // 6 learned proposal, 7 ASI extrapolation
+    static constexpr int kGraphs = 8;
+    cudaGraphExec_t graph_execs[kGraphs] = {};
+    cudaGraph_t graphs[kGraphs] = {};
     // learned proposal: the last four source updates, the network, the state before the
     // iteration that carries a proposal (for the rollback)
     double* hist = nullptr;         // n_src x 4 x 5, oldest first
@@ -291,13 +293,19 @@ struct agis_ctx {
     float* prop_X = nullptr;
     float* prop_Y = nullptr;
     double* prop_sigma = nullptr;
-    double* prop_corr = nullptr;
+    double* prop_corr = nullptr;    // correction in tangent units (proposal or ASI)
     int prop_every = 0;
     int since_prop = 1 << 30;
     bool prop_pending = false;
     double chi2_before_prop = 0.0;
     double *snap_src = nullptr, *snap_att = nullptr, *snap_cal = nullptr, *snap_hist = nullptr;
     int snap_hist_count = 0;
+    // accelerated simple iteration: sample stride (0 off), clamp of lambda, the sample's keys
+    // and the estimate [median, lambda, factor, count]
+    int asi_stride = 0;
+    double asi_lam_max = 0.9;
+    unsigned long long* asi_keys = nullptr;
+    double* asi_est = nullptr;
     bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
@@ -448,6 +456,16 @@ void enqueue_proposal(agis_ctx* c) {
                          c->prop_sigma, c->stream);
     launch_mlp_forward(c->prop_packed, c->prop_X, c->n_src, c->prop_Y, c->stream);
     launch_prop_apply(c->n_src, c->prop_Y, c->prop_sigma, c->src, c->prop_corr, c->stream);
+    if (c->mixed)
+        launch_mix_prop(c->n_src, c->src_off, c->ms, c->prop_corr, c->stream);
+    else
+        launch_prop_rec(c->n_src, c->src_off, c->scratch, c->rec, c->prop_corr, c->stream);
+}
+// ASI after the S block: lambda from the sample's parallax-update ratios, sources +=
+// (f - 1) d, and the residuals that A and C read -= A (f - 1) d
+void enqueue_asi(agis_ctx* c) {
+    launch_asi(c->n_src, c->asi_stride, c->hist, c->asi_lam_max, c->asi_keys, c->asi_est, c->so.d, c->src,
+               c->prop_corr, c->stream);
     if (c->mixed)
         launch_mix_prop(c->n_src, c->src_off, c->ms, c->prop_corr, c->stream);
     else
@@ -909,6 +927,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
         for (int b = 0; b < agis_ctx::kGraphs; b++) {
             if (b == 4 && !c->mixed) continue;
             if (b == 6 && !c->prop_packed) continue;
+            if (b == 7 && !c->asi_keys) continue;
             AGIS_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             if (b == 0) enqueue_s_pass(c, false);
             if (b == 4) enqueue_s_pass(c, true);
@@ -917,6 +936,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             if (b == 2) enqueue_c(c);
             if (b == 3 && c->ref) enqueue_frame(c, nullptr, c->n_src);
             if (b == 6) enqueue_proposal(c);
+            if (b == 7) enqueue_asi(c);
             AGIS_CU(c, cudaStreamEndCapture(c->stream, &c->graphs[b]), "end capture");
             AGIS_CU(c, cudaGraphInstantiate(&c->graph_execs[b], c->graphs[b], 0), "instantiate graph");
         }
@@ -931,9 +951,11 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
         if (b == 2) enqueue_c(c);
         if (b == 3) enqueue_frame(c, nullptr, c->n_src);
         if (b == 6) enqueue_proposal(c);
+        if (b == 7) enqueue_asi(c);
         return cuda_check(c, cudaGetLastError(), "block launch");
     };
     const bool proposals = c->prop_every > 0 && (mask & 1);
+    const bool asi = c->asi_stride > 0 && (mask & 1);
     auto snapshot = [&](bool save) -> int {
         const size_t ns = 5 * (size_t)c->n_src, na = 4 * (size_t)c->n_coef, nc = (size_t)c->n_cal,
                      nh = 20 * (size_t)c->n_src;
@@ -1001,6 +1023,14 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             c->since_prop = 0;
             prop_state = 1;
         }
+        // ASI needs the updates of two S blocks; not on top of a proposal
+        const bool asi_now = asi && prop_state != 1 && c->hist_count >= 2;
+        if (asi_now) {
+            AGIS_TRY(run_block(7));
+            AGIS_CU(c, cudaMemcpyAsync(c->hstat + 24, c->asi_est, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                       c->stream),
+                    "stats");
+        }
         AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
         if (mask & 2) AGIS_TRY(run_block(1));
         AGIS_CU(c, cudaEventRecord(c->ev[10], c->stream), "event");
@@ -1030,6 +1060,12 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             it.c.elapsed_ms = elapsed(c, 10, 11);
             it.elapsed_ms = elapsed(c, 8, 11);
             it.proposal = prop_state;
+            it.asi_factor = 1.0;
+            if (asi_now) {
+                it.asi_lambda = c->hstat[24];
+                it.asi_factor = c->hstat[26];
+                it.asi_n = (int32_t)llround(c->hstat[27]);
+            }
         }
         if ((mask & 1) && !std::isfinite(chi2)) return fail(c, AGIS_E_NONFINITE, "non-finite chi^2");
         if (n_done) *n_done = k + 1;
@@ -1103,6 +1139,16 @@ int agis_get_source_stats(agis_ctx* c, double* stats_out, double* cov_out) {
     return AGIS_OK;
 }
 
+static void drop_graphs(agis_ctx* c) {
+    for (int b = 0; b < agis_ctx::kGraphs; b++) {
+        if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
+        if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
+        c->graph_execs[b] = nullptr;
+        c->graphs[b] = nullptr;
+    }
+    c->graphs_ready = false;
+}
+
 int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
     if (!c) return AGIS_E_INVALID;
     if (!params) {
@@ -1119,7 +1165,7 @@ int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
         AGIS_TRY(dalloc(c, &c->prop_X, (size_t)AGIS_MLP_N_IN * c->n_src));
         AGIS_TRY(dalloc(c, &c->prop_Y, (size_t)AGIS_MLP_N_OUT * c->n_src));
         AGIS_TRY(dalloc(c, &c->prop_sigma, c->n_src));
-        AGIS_TRY(dalloc(c, &c->prop_corr, 5 * (size_t)c->n_src));
+        if (!c->prop_corr) AGIS_TRY(dalloc(c, &c->prop_corr, 5 * (size_t)c->n_src));
         AGIS_TRY(dalloc(c, &c->snap_src, 5 * (size_t)c->n_src));
         AGIS_TRY(dalloc(c, &c->snap_att, 4 * (size_t)c->n_coef));
         AGIS_TRY(dalloc(c, &c->snap_cal, c->n_cal));
@@ -1135,14 +1181,26 @@ int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
     c->prop_every = every;
     c->prop_pending = false;
     c->since_prop = 1 << 30;
-    // the per-block graphs are captured again with the proposal graph
-    for (int b = 0; b < agis_ctx::kGraphs; b++) {
-        if (c->graph_execs[b]) cudaGraphExecDestroy(c->graph_execs[b]);
-        if (c->graphs[b]) cudaGraphDestroy(c->graphs[b]);
-        c->graph_execs[b] = nullptr;
-        c->graphs[b] = nullptr;
+    drop_graphs(c);   // captured again with the proposal graph
+    return AGIS_OK;
+}
+
+int agis_set_asi(agis_ctx* c, int32_t stride, double lambda_max) {
+    if (!c) return AGIS_E_INVALID;
+    if (stride <= 0) {
+        c->asi_stride = 0;
+        return AGIS_OK;
     }
-    c->graphs_ready = false;
+    if (!(lambda_max >= 0.0 && lambda_max < 1.0)) return fail(c, AGIS_E_INVALID, "lambda_max outside [0, 1)");
+    if (!c->asi_keys) {
+        const size_t n_s = std::max<size_t>(1, ((size_t)c->n_src + stride - 1) / stride);
+        AGIS_TRY(dalloc(c, &c->asi_keys, std::max<size_t>(n_s, (size_t)c->n_src)));
+        AGIS_TRY(dalloc(c, &c->asi_est, 4));
+        if (!c->prop_corr) AGIS_TRY(dalloc(c, &c->prop_corr, 5 * (size_t)c->n_src));
+    }
+    c->asi_stride = stride;
+    c->asi_lam_max = lambda_max;
+    drop_graphs(c);   // the stride and the clamp are captured in the ASI graph
     return AGIS_OK;
 }
 

@@ -358,7 +358,120 @@ __global__ void k_prop_rec(int32_t n_src, const int64_t* __restrict__ src_off, c
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// accelerated simple iteration (Sect. 4.7)
+// ---------------------------------------------------------------------------------------
+// order-preserving map of a double onto uint64 (negative values: all bits flipped; others:
+// sign bit set), and back
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    const unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+constexpr int kAsiThreads = 1024;
+
+// One block.  r_j = d1[i] / d0[i] for the parallax of sample source i = j * stride (rows
+// of ld doubles, parallax at 2); the lower median of the finite ratios by an exact radix
+// select over their order-preserving keys, 8 digits of 8 bits.  out: [median, lambda
+// clamped to [0, lam_max], 1 / (1 - lambda), count of ratios].
+__global__ void __launch_bounds__(kAsiThreads) k_asi_lambda(int32_t n_src, int32_t stride,
+                                                            const double* __restrict__ d0p,
+                                                            const double* __restrict__ d1p, int ld, double lam_max,
+                                                            unsigned long long* __restrict__ keys,
+                                                            double* __restrict__ out) {
+    __shared__ unsigned int bins[256];
+    __shared__ unsigned int s_count;
+    __shared__ unsigned long long s_prefix, s_mask;
+    __shared__ unsigned int s_rank;
+    const int n_s = (n_src + stride - 1) / stride;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    unsigned int cnt = 0;
+    for (int j = threadIdx.x; j < n_s; j += kAsiThreads) {
+        const size_t row = (size_t)ld * j * stride + 2;
+        const double d0 = d0p[row], d1 = d1p[row];
+        const double r = d0 != 0.0 ? d1 / d0 : 0.0;
+        const bool ok = d0 != 0.0 && isfinite(r);
+        keys[j] = ok ? ord_key(r) : ~0ull;   // invalid ratios sort after every finite one
+        cnt += ok ? 1u : 0u;
+    }
+    atomicAdd(&s_count, cnt);
+    if (threadIdx.x == 0) {
+        s_prefix = 0ull;
+        s_mask = 0ull;
+    }
+    __syncthreads();
+    const unsigned int n_ok = s_count;
+    if (n_ok == 0) {
+        if (threadIdx.x == 0) {
+            out[0] = 0.0;
+            out[1] = 0.0;
+            out[2] = 1.0;
+            out[3] = 0.0;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) s_rank = (n_ok - 1) / 2;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += kAsiThreads) bins[b] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix, mask = s_mask;
+        for (int j = threadIdx.x; j < n_s; j += kAsiThreads) {
+            const unsigned long long k = keys[j];
+            if ((k & mask) == prefix) atomicAdd(&bins[(unsigned int)(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int rank = s_rank, b = 0;
+            for (; b < 255; b++) {
+                if (rank < bins[b]) break;
+                rank -= bins[b];
+            }
+            s_rank = rank;
+            s_prefix = prefix | ((unsigned long long)b << shift);
+            s_mask = mask | (255ull << shift);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double med = key_value(s_prefix);
+        const double lam = fmin(fmax(med, 0.0), lam_max);
+        out[0] = med;
+        out[1] = lam;
+        out[2] = 1.0 / (1.0 - lam);
+        out[3] = (double)n_ok;
+    }
+}
+
+// sources += (f - 1) d (alpha* turned into alpha with cos(delta)); the correction is kept in
+// tangent units for the residual update
+__global__ void k_asi_apply(int32_t n_src, const double* __restrict__ d, const double* __restrict__ est,
+                            double* __restrict__ src, double* __restrict__ corr) {
+    const double g = est[2] - 1.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        double* s = src + 5 * (size_t)i;
+        double c[5];
+        for (int k = 0; k < 5; k++) {
+            const double v = g * d[5 * (size_t)i + k];
+            c[k] = isfinite(v) ? v : 0.0;
+        }
+        s[0] += c[0] / cos(s[1]);
+        for (int k = 1; k < 5; k++) s[k] += c[k];
+        for (int k = 0; k < 5; k++) corr[5 * (size_t)i + k] = c[k];
+    }
+}
+
 // host launchers
+void launch_asi(int32_t n_src, int32_t stride, const double* hist, double lam_max, unsigned long long* keys,
+                double* est, const double* d, double* src, double* corr, cudaStream_t s) {
+    // the history holds the last four updates, oldest first: the previous at 10, the latest at 15
+    k_asi_lambda<<<1, kAsiThreads, 0, s>>>(n_src, stride, hist + 10, hist + 15, 20, lam_max, keys, est);
+    k_asi_apply<<<grid_of(n_src, 256, 152 * 16), 256, 0, s>>>(n_src, d, est, src, corr);
+}
 void launch_hist_push(int32_t n_src, const double* d, double* hist, cudaStream_t s) {
     k_hist_push<<<grid_of(n_src, 256, 152 * 16), 256, 0, s>>>(n_src, d, hist);
 }
@@ -452,6 +565,17 @@ int agis_proposal_targets(const double* src_k, const double* src_ref, const doub
     agis::k_prop_targets<<<agis::grid_of(n, 256, 152 * 16), 256, 0, (cudaStream_t)stream>>>(n, src_k, src_ref, sigma,
                                                                                              T);
     return mlp_launch_status("agis_proposal_targets");
+}
+
+int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, int32_t stride, double lambda_max,
+                      void* scratch, double* est, void* stream) {
+    if (!d_prev || !d_cur || !scratch || !est || n_src < 1 || stride < 1 || !(lambda_max >= 0.0 && lambda_max < 1.0)) {
+        agis::set_thread_error("agis_asi_estimate: invalid argument");
+        return AGIS_E_INVALID;
+    }
+    agis::k_asi_lambda<<<1, agis::kAsiThreads, 0, (cudaStream_t)stream>>>(
+        n_src, stride, d_prev, d_cur, 5, lambda_max, (unsigned long long*)scratch, est);
+    return mlp_launch_status("agis_asi_estimate");
 }
 
 }  // extern "C"
