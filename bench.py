@@ -46,7 +46,7 @@ MIX_PASS_BYTES = 8 + 16 + 4 + 8 + 8
 # DRAM bytes per observation (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
 # of 2.47e7 observations, scaled per observation; profiles/k_*_kernels_30k.md): the S block of
 # the FP64 form (observation pass + solves) and the mixed form's linearized pass
-TRAFFIC_PER_OBS = {"fp64_s_block": 866.0, "mixed_correct": 94.5}
+TRAFFIC_PER_OBS = {"fp64_s_block": 866.0, "mixed_correct": 47.6}
 
 
 def parse():
@@ -63,6 +63,8 @@ def parse():
                     help="form timed for the headline value (the other is reported beside it)")
     ap.add_argument("--refresh-every", type=int, default=8, help="mixed form: full FP64 evaluation period")
     ap.add_argument("--single-form", action="store_true", help="time only the --precision form")
+    ap.add_argument("--tune-iters", type=int, default=20,
+                    help="iterations of the launch-shape autotuner before the warm-up (0: default shapes)")
     ap.add_argument("--knot-dt-s", type=int, default=0, help="override the attitude knot interval (testing)")
     ap.add_argument("--convergence", action="store_true",
                     help="wall time to 1 uas RMS of both forms against an FP64 reference solution")
@@ -235,8 +237,9 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def time_form(agis, ds, stream, cfg, steps, warmup, local, dist):
-    """Device-resident timing of `steps` iterations after `warmup` untimed ones."""
+def time_form(agis, ds, stream, cfg, steps, warmup, local, dist, tune_iters=0):
+    """Device-resident timing of `steps` iterations after `warmup` untimed ones; before the
+    warm-up, up to `tune_iters` iterations of the launch-shape autotuner (untimed)."""
     import torch
     # the context copies the observations into HBM at set-up; the timed iterations read only
     # device-resident data
@@ -247,6 +250,14 @@ def time_form(agis, ds, stream, cfg, steps, warmup, local, dist):
                   stream=stream.cuda_stream)
     t_init = time.perf_counter() - t
     del obs_h
+    tuning = None
+    if tune_iters > 0:
+        t = time.perf_counter()
+        n_t, rep = g.autotune(tune_iters)
+        tuning = {"iterations": n_t, "seconds": round(time.perf_counter() - t, 2),
+                  "shapes": {k: [v["a"], v["b"]] for k, v in rep.items() if v["n_tried"]},
+                  "block_ms_default_vs_kept": {k: [round(v["default_ms"], 3), round(v["best_ms"], 3)]
+                                               for k, v in rep.items() if v["n_tried"]}}
     g.iterate(warmup)
     # flush-free timing: the inputs (>= tens of GB) are far larger than the 129 MB L2
     sampler = ClockSampler(local)
@@ -271,7 +282,7 @@ def time_form(agis, ds, stream, cfg, steps, warmup, local, dist):
     full = [it for it in its if it["s"]["full_eval"]]
     lin = [it for it in its if not it["s"]["full_eval"]]
     med = lambda xs: float(np.median(xs)) if xs else None
-    return {"ms": ms, "t_init": t_init, "clocks": clocks, "n_full_eval": len(full),
+    return {"ms": ms, "t_init": t_init, "clocks": clocks, "n_full_eval": len(full), "tuning": tuning,
             "s_ms": med([it["s"]["elapsed_ms"] for it in its]), "a_ms": med([it["a"]["elapsed_ms"] for it in its]),
             "c_ms": med([it["c"]["elapsed_ms"] for it in its]),
             "pass_full_ms": med([it["s"]["pass_ms"] for it in full]),
@@ -453,9 +464,10 @@ def main():
     # the full FP64 evaluation at its share
     cyc = max(1, args.refresh_every)
     steps_of = {"fp64": args.steps, "mixed": cyc * max(1, -(-args.steps // cyc))}
-    res = {head: time_form(agis, ds, stream, cfgs[head], steps_of[head], args.warmup, local, dist)}
+    res = {head: time_form(agis, ds, stream, cfgs[head], steps_of[head], args.warmup, local, dist, args.tune_iters)}
     if not args.single_form:
-        res[other] = time_form(agis, ds, stream, cfgs[other], steps_of[other], args.warmup, local, dist)
+        res[other] = time_form(agis, ds, stream, cfgs[other], steps_of[other], args.warmup, local, dist,
+                               args.tune_iters)
     r = res[head]
     value = world * ds.n_obs / (r["ms"] * 1e-3)
     # ---- end to end through the C ABI from pinned host buffers
@@ -474,6 +486,8 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         ge = agis.Agis(ds.geometry, cfgs[head], host, src0, att0, cal0, src_ref=ref, stream=stream.cuda_stream)
+        if r["tuning"]:
+            ge.set_tuning(r["tuning"]["shapes"])
         ge.iterate(1)
         ge.sources(out=out_src.numpy())
         torch.cuda.synchronize()
@@ -501,7 +515,8 @@ def main():
         achieved = MIX_PASS_BYTES * ds.n_obs / (x["pass_lin_ms"] * 1e-3) / 1e9
         return {"bound": "hbm", "kernel": "k_mix_correct (linearized observation pass)", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": TRAFFIC_PER_OBS["mixed_correct"] * ds.n_obs,
+                "traffic": (TRAFFIC_PER_OBS["mixed_correct"] * ds.n_obs
+                            if TRAFFIC_PER_OBS["mixed_correct"] is not None else None),
                 "peak_source": hbm_src, "bytes_per_obs": MIX_PASS_BYTES}
 
     def summary(name, x):
@@ -509,7 +524,7 @@ def main():
              "block_ms": {"S": x["s_ms"], "S_pass_full": x["pass_full_ms"], "S_pass_linearized": x["pass_lin_ms"],
                           "S_solve": x["solve_ms"], "A": x["a_ms"], "C": x["c_ms"],
                           "rest": x["ms"] - x["s_ms"] - x["a_ms"] - x["c_ms"]},
-             "t_init_s": round(x["t_init"], 2), "clocks": x["clocks"]}
+             "t_init_s": round(x["t_init"], 2), "clocks": x["clocks"], "autotune": x["tuning"]}
         if name == "mixed":
             d.update({"dtype": "f32+f64", "refresh_every": args.refresh_every, "full_evals_timed": x["n_full_eval"],
                       "roofline": mixed_roofline(x)})
@@ -525,7 +540,8 @@ def main():
                    "n_src": ds.n_src, "n_coef": ds.n_coef, "n_cal": ds.n_cal, "precision": head,
                    "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "t_generate_s": round(t_gen, 1), "t_init_s": round(r["t_init"], 2)},
+                   "t_generate_s": round(t_gen, 1), "t_init_s": round(r["t_init"], 2),
+                   "autotune": r["tuning"]},
         "e2e": ({"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
                 if e2e is not None else None),
         "gpu_launches": (KERNELS_PER_STEP[head][0] * r["n_full_eval"] +

@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 4
+#define AGIS_ABI_VERSION 5
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -319,6 +319,57 @@ int agis_set_asi(agis_ctx* ctx, int32_t stride, double lambda_max);
  * AGIS_E_CUDA. */
 int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, int32_t stride, double lambda_max,
                       void* scratch, double* est, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Launch-shape autotuner (iteration control)
+ *
+ * Knobs and their parameters (a, b):
+ *   AGIS_KNOB_OBS_PASS    observation pass (FP64 model in the FP64 form, the linearized
+ *                         correction in the mixed form): a threads per block (128, 256),
+ *                         b blocks per SM of the grid-stride grid (1..64)
+ *   AGIS_KNOB_SRC_BATCH   FP64 form, per-source solves: a sources per work fetch of the
+ *                         persistent kernel (1..32; 0: n_src / 2432 within 1..32); b unused
+ *   AGIS_KNOB_MIX_SUMS    mixed form, S-block sums and final pass: a warps per block
+ *                         (2, 4, 8), b blocks per SM (1..64)
+ *   AGIS_KNOB_MIX_SOLVE5  mixed form, 5x5 solves (a thread per source): a threads per block
+ *                         (64, 128, 256); b unused
+ *   AGIS_KNOB_ATT_ACCUM   A-block accumulation (a warp per knot interval): b blocks per SM
+ *                         (1..64; 0: 32 in the FP64 form, 64 in the mixed form); a unused
+ *   AGIS_KNOB_CAL_ACCUM   C-block accumulation (a warp per parameter): a threads per block
+ *                         (128, 256), b blocks per SM (1..64)
+ * Every kernel a knob shapes gives each observation, source, knot interval or calibration
+ * parameter to one thread or one warp with the same arithmetic whatever the shape, so the
+ * solution does not depend on the knobs (bit for bit).
+ *
+ * agis_autotune runs up to max_iter S[ACG] iterations, exactly as agis_iterate would (they
+ * advance the solution; the learned proposal and ASI pause meanwhile, and the blocks run
+ * without graph capture).  Each iteration gives each timed block (S observation pass, S
+ * solves, A, C) one candidate shape of one of its knobs; the device time of the block (CUDA
+ * events) rates it.  The mixed form rates its observation pass only in iterations that use
+ * the linearized correction.  When every candidate of a knob has been rated, the fastest is
+ * kept; the candidates include the default.  out (may be NULL): AGIS_N_KNOBS entries in knob
+ * order; *n_done: iterations run.  Errors: AGIS_E_INVALID, AGIS_E_CUDA, AGIS_E_NONFINITE.
+ *
+ * agis_get_tuning / agis_set_tuning read and set the shapes (for instance to reuse a tuning
+ * on another context of the same workload); set validates every value against the ranges
+ * above and changes nothing on AGIS_E_INVALID. */
+#define AGIS_KNOB_OBS_PASS 0
+#define AGIS_KNOB_SRC_BATCH 1
+#define AGIS_KNOB_MIX_SUMS 2
+#define AGIS_KNOB_MIX_SOLVE5 3
+#define AGIS_KNOB_ATT_ACCUM 4
+#define AGIS_KNOB_CAL_ACCUM 5
+#define AGIS_N_KNOBS 6
+typedef struct agis_tune_entry {
+    int32_t knob;                /* AGIS_KNOB_*                                          */
+    int32_t a, b;                /* the shape (meaning per knob, above)                  */
+    int32_t n_tried;             /* candidates rated (0: the knob does not apply)        */
+    double best_ms;              /* device time of the block with the kept shape         */
+    double default_ms;           /* ... with the default shape (-1: not rated)           */
+} agis_tune_entry;
+int agis_autotune(agis_ctx* ctx, int32_t max_iter, int32_t* n_done, agis_tune_entry* out);
+int agis_get_tuning(const agis_ctx* ctx, agis_tune_entry* out);
+int agis_set_tuning(agis_ctx* ctx, const agis_tune_entry* in, int32_t n);
 
 #ifdef __cplusplus
 }

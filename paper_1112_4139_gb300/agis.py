@@ -19,7 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 4  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 5  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -27,8 +27,10 @@ EXPORTS = (
     "agis_get_source_stats", "agis_get_sizes", "agis_get_kernel_times", "agis_destroy", "agis_last_error",
     "agis_abi_version", "agis_source_update_static", "agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad",
     "agis_mlp_adam", "agis_proposal_targets", "agis_set_proposal", "agis_get_proposal_features",
-    "agis_copy_sources_device", "agis_set_asi", "agis_asi_estimate",
+    "agis_copy_sources_device", "agis_set_asi", "agis_asi_estimate", "agis_autotune", "agis_get_tuning",
+    "agis_set_tuning",
 )
+KNOBS = ("obs_pass", "src_batch", "mix_sums", "mix_solve5", "att_accum", "cal_accum")  # AGIS_KNOB_* order
 STATIC_MAX_OBS = 16384
 MLP_N_IN, MLP_N_OUT, MLP_N_PARAMS, MLP_PACKED_BYTES = 22, 5, 5957, 16032
 
@@ -68,6 +70,11 @@ class BlockStats(C.Structure):
         return dict(chi2=self.chi2, q_sum=self.q_sum, nu_sum=self.nu_sum, n_out=self.n_out,
                     rank_defect=self.rank_defect, d_rms=list(self.d_rms), elapsed_ms=self.elapsed_ms,
                     pass_ms=self.pass_ms, full_eval=self.full_eval)
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("knob", C.c_int32), ("a", C.c_int32), ("b", C.c_int32), ("n_tried", C.c_int32),
+                ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class IterStats(C.Structure):
@@ -129,9 +136,12 @@ def load():
         lib.agis_copy_sources_device.argtypes = [V, P]
         lib.agis_set_asi.argtypes = [V, C.c_int32, C.c_double]
         lib.agis_asi_estimate.argtypes = [P, P, C.c_int32, C.c_int32, C.c_double, P, P, V]
+        lib.agis_autotune.argtypes = [V, C.c_int32, C.POINTER(C.c_int32), P]
+        lib.agis_get_tuning.argtypes = [V, P]
+        lib.agis_set_tuning.argtypes = [V, P, C.c_int32]
         for f in ("agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad", "agis_mlp_adam", "agis_proposal_targets",
                   "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device", "agis_set_asi",
-                  "agis_asi_estimate"):
+                  "agis_asi_estimate", "agis_autotune", "agis_get_tuning", "agis_set_tuning"):
             getattr(lib, f).restype = I
         if lib.agis_abi_version() != ABI_VERSION:
             raise RuntimeError(f"libagis.so has ABI {lib.agis_abi_version()}, this binding {ABI_VERSION}: rebuild")
@@ -307,6 +317,27 @@ class Agis:
     def copy_sources_device(self, out):
         self._check(self._lib.agis_copy_sources_device(self.ctx, _ptr(out)))
 
+    # launch-shape autotuner
+    def autotune(self, max_iter=16):
+        """Run up to max_iter iterations rating candidate launch shapes; returns (iterations
+        run, {knob: dict(a, b, n_tried, best_ms, default_ms)})."""
+        arr = (TuneEntry * 6)()
+        done = C.c_int32(0)
+        self._check(self._lib.agis_autotune(self.ctx, int(max_iter), C.byref(done), C.cast(arr, C.c_void_p)))
+        return done.value, _tune_dict(arr)
+
+    def tuning(self):
+        arr = (TuneEntry * 6)()
+        self._check(self._lib.agis_get_tuning(self.ctx, C.cast(arr, C.c_void_p)))
+        return _tune_dict(arr)
+
+    def set_tuning(self, shapes):
+        """shapes: {knob name: (a, b)}."""
+        arr = (TuneEntry * max(1, len(shapes)))()
+        for i, (name, (a, b)) in enumerate(shapes.items()):
+            arr[i].knob, arr[i].a, arr[i].b = KNOBS.index(name), int(a), int(b)
+        self._check(self._lib.agis_set_tuning(self.ctx, C.cast(arr, C.c_void_p), len(shapes)))
+
     # accelerated simple iteration
     def set_asi(self, stride=16, lambda_max=0.9):
         """Extrapolate the source update of each iteration by 1/(1 - lambda), lambda from the
@@ -348,6 +379,11 @@ def mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream
 def proposal_targets(src_k, src_ref, sigma, T, stream=None):
     _mlp_call("agis_proposal_targets", _ptr(src_k), _ptr(src_ref), _ptr(sigma), int(src_k.shape[0]), _ptr(T),
               _stream(stream))
+
+
+def _tune_dict(arr):
+    return {KNOBS[e.knob]: dict(a=e.a, b=e.b, n_tried=e.n_tried, best_ms=e.best_ms, default_ms=e.default_ms)
+            for e in arr}
 
 
 def asi_estimate(d_prev, d_cur, stride, lambda_max, scratch, est, stream=None):

@@ -15,32 +15,33 @@ namespace agis {
 void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
-                     cudaStream_t stream);
+                     const Shapes& sh, cudaStream_t stream);
 void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
                          const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
-                         int* work_counter, int n_blocks, cudaStream_t stream);
+                         int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream);
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
-                      int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s);
+                      int n_iv, const ObsRec* rec, const double* att, double* blk, const Shapes& sh, cudaStream_t s);
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
                       cudaStream_t s);
 void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
-                     const double* att, const double* cal, MixS* ms, MixT* mt, double* geo, float* d_att,
-                     float2* d_cal, int n_coef, int n_cal, cudaStream_t s);
+                     const double* att, const double* cal, const MixObs& mo, double* geo, float* d_att,
+                     float2* d_cal, int n_coef, int n_cal, const Shapes& sh, cudaStream_t s);
 void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_nal, const int32_t* src_order,
-                      int32_t n_src, const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s);
+                      int32_t n_src, const SrcOutPtrs& out, const MixObs& mo, const MixSrcWork& w,
+                      const Shapes& sh, cudaStream_t s);
 void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
-                          const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
-                          double* blk, cudaStream_t s);
-void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
-                    double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s);
-void launch_mix_rw(int64_t n, const uint32_t* perm, const MixS* ms, double* R, double* W, cudaStream_t s);
-void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const double* corr, cudaStream_t s);
+                          const int64_t* ivl_off, int n_iv, const MixObs& mo, const double* att, double* blk,
+                          const Shapes& sh, cudaStream_t s);
+void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixObs& mo,
+                    double* dtil, int* rd, double* cal, float2* d_cal, const Shapes& sh, cudaStream_t s);
+void launch_mix_rw(int64_t n, const uint32_t* perm, const MixObs& mo, double* R, double* W, cudaStream_t s);
+void launch_mix_prop(int32_t n_src, const int64_t* src_off, const MixObs& mo, const double* corr, cudaStream_t s);
 void launch_hist_push(int32_t n_src, const double* d, double* hist, cudaStream_t s);
 void launch_prop_features(int32_t n_src, const double* hist, const int64_t* src_off, const double* src,
                           double sin_obl, double cos_obl, float* X, double* sigma, cudaStream_t s);
@@ -52,7 +53,7 @@ void launch_prop_rec(int32_t n_src, const int64_t* src_off, const double* scratc
 void launch_asi(int32_t n_src, int32_t stride, const double* hist, double lam_max, unsigned long long* keys,
                 double* est, const double* d, double* src, double* corr, cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
-                double* dtil, int* rd, double* cal, cudaStream_t s);
+                double* dtil, int* rd, double* cal, const Shapes& sh, cudaStream_t s);
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
                   double* att, double* partial, int n_part, double tol, double* eo, cudaStream_t s);
 void launch_src_stats(int n_src, const double* chi2, const double* q, const int* nu, const int* nout, const int* rdf,
@@ -232,8 +233,7 @@ struct agis_ctx {
     ObsRec* rec = nullptr;
     // mixed-precision form: records, updates since the last S block, refresh bookkeeping
     bool mixed = false;
-    MixS* ms = nullptr;
-    MixT* mt = nullptr;
+    MixObs mo{};
     float* d_att = nullptr;
     float2* d_cal = nullptr;
     MixSrcWork mw{};
@@ -306,6 +306,8 @@ struct agis_ctx {
     double asi_lam_max = 0.9;
     unsigned long long* asi_keys = nullptr;
     double* asi_est = nullptr;
+    // launch shapes (defaults until agis_autotune or agis_set_tuning)
+    Shapes sh;
     bool graphs_ready = false;
     bool own_stream = false;
     double* tmpS = nullptr;
@@ -434,17 +436,19 @@ void s_done(agis_ctx* c, bool refresh) {
 void enqueue_s_pass(agis_ctx* c, bool refresh) {
     if (c->mixed)
         launch_mix_pass(c->G, refresh, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src,
-                        c->att, c->cal, c->ms, c->mt, c->sgeo, c->d_att, c->d_cal, c->n_coef, c->n_cal, c->stream);
+                        c->att, c->cal, c->mo, c->sgeo, c->d_att, c->d_cal, c->n_coef, c->n_cal, c->sh,
+                        c->stream);
     else
         launch_obs_pass(c->G, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
-                        c->cal, c->rec, c->sgeo, c->scratch, c->stream);
+                        c->cal, c->rec, c->sgeo, c->scratch, c->sh, c->stream);
 }
 void enqueue_s_solve(agis_ctx* c) {
     if (c->mixed)
-        launch_mix_solve(c->st, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->ms, c->mw, c->stream);
+        launch_mix_solve(c->st, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->mo, c->mw, c->sh,
+                         c->stream);
     else
         launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
-                            c->work, c->n_sblocks, c->stream);
+                            c->work, c->n_sblocks, c->sh, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
@@ -457,7 +461,7 @@ void enqueue_proposal(agis_ctx* c) {
     launch_mlp_forward(c->prop_packed, c->prop_X, c->n_src, c->prop_Y, c->stream);
     launch_prop_apply(c->n_src, c->prop_Y, c->prop_sigma, c->src, c->prop_corr, c->stream);
     if (c->mixed)
-        launch_mix_prop(c->n_src, c->src_off, c->ms, c->prop_corr, c->stream);
+        launch_mix_prop(c->n_src, c->src_off, c->mo, c->prop_corr, c->stream);
     else
         launch_prop_rec(c->n_src, c->src_off, c->scratch, c->rec, c->prop_corr, c->stream);
 }
@@ -467,17 +471,17 @@ void enqueue_asi(agis_ctx* c) {
     launch_asi(c->n_src, c->asi_stride, c->hist, c->asi_lam_max, c->asi_keys, c->asi_est, c->so.d, c->src,
                c->prop_corr, c->stream);
     if (c->mixed)
-        launch_mix_prop(c->n_src, c->src_off, c->ms, c->prop_corr, c->stream);
+        launch_mix_prop(c->n_src, c->src_off, c->mo, c->prop_corr, c->stream);
     else
         launch_prop_rec(c->n_src, c->src_off, c->scratch, c->rec, c->prop_corr, c->stream);
 }
 void enqueue_a(agis_ctx* c) {
     if (c->mixed)
-        launch_mix_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, c->ms, c->mt,
-                             c->att, c->blk, c->stream);
+        launch_mix_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, c->mo,
+                             c->att, c->blk, c->sh, c->stream);
     else
         launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
-                         c->rec, c->att, c->blk, c->stream);
+                         c->rec, c->att, c->blk, c->sh, c->stream);
     launch_att_solve(c->n_seg, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
                      c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->mixed ? c->d_att : nullptr,
                      c->stream);
@@ -485,11 +489,11 @@ void enqueue_a(agis_ctx* c) {
 }
 void enqueue_c(agis_ctx* c) {
     if (c->mixed)
-        launch_mix_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->ms, c->dtil, c->cal_rd, c->cal, c->d_cal,
-                       c->stream);
+        launch_mix_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->mo, c->dtil, c->cal_rd, c->cal, c->d_cal,
+                       c->sh, c->stream);
     else
         launch_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->rec, c->st.pivot_tol, c->dtil,
-                   c->cal_rd, c->cal, c->stream);
+                   c->cal_rd, c->cal, c->sh, c->stream);
     launch_int_sum(c->n_cal, c->cal_rd, c->isum + 1, c->stream);
 }
 void enqueue_frame(agis_ctx* c, const int32_t* subset, int n) {
@@ -513,6 +517,67 @@ void fill_s_stats(agis_ctx* c, const double* h, agis_block_stats* out) {
 // -----------------------------------------------------------------------------------------
 // ABI
 // -----------------------------------------------------------------------------------------
+// --- launch-shape autotuner --------------------------------------------------------------
+namespace {
+struct ShapeCand {
+    int a, b;
+};
+void knob_get(const Shapes& sh, int k, int& a, int& b) {
+    switch (k) {
+        case AGIS_KNOB_OBS_PASS: a = sh.obs_threads; b = sh.obs_bps; break;
+        case AGIS_KNOB_SRC_BATCH: a = sh.src_batch; b = 0; break;
+        case AGIS_KNOB_MIX_SUMS: a = sh.sums_warps; b = sh.sums_bps; break;
+        case AGIS_KNOB_MIX_SOLVE5: a = sh.solve5_threads; b = 0; break;
+        case AGIS_KNOB_ATT_ACCUM: a = 0; b = sh.att_bps; break;
+        default: a = sh.cal_threads; b = sh.cal_bps; break;
+    }
+}
+void knob_set(Shapes& sh, int k, int a, int b) {
+    switch (k) {
+        case AGIS_KNOB_OBS_PASS: sh.obs_threads = a; sh.obs_bps = b; break;
+        case AGIS_KNOB_SRC_BATCH: sh.src_batch = a; break;
+        case AGIS_KNOB_MIX_SUMS: sh.sums_warps = a; sh.sums_bps = b; break;
+        case AGIS_KNOB_MIX_SOLVE5: sh.solve5_threads = a; break;
+        case AGIS_KNOB_ATT_ACCUM: sh.att_bps = b; break;
+        default: sh.cal_threads = a; sh.cal_bps = b; break;
+    }
+}
+bool knob_valid(int k, int a, int b) {
+    const bool bps = b >= 1 && b <= 64;
+    switch (k) {
+        case AGIS_KNOB_OBS_PASS: return (a == 128 || a == 256) && bps;
+        case AGIS_KNOB_SRC_BATCH: return a >= 0 && a <= 32;
+        case AGIS_KNOB_MIX_SUMS: return (a == 2 || a == 4 || a == 8) && bps;
+        case AGIS_KNOB_MIX_SOLVE5: return a == 64 || a == 128 || a == 256;
+        case AGIS_KNOB_ATT_ACCUM: return b == 0 || bps;
+        case AGIS_KNOB_CAL_ACCUM: return (a == 128 || a == 256) && bps;
+        default: return false;
+    }
+}
+// candidate shapes of a knob, the default first (empty: the knob does not apply to the form)
+std::vector<ShapeCand> knob_candidates(int k, bool mixed) {
+    switch (k) {
+        case AGIS_KNOB_OBS_PASS:
+            if (mixed) return {{256, 64}, {256, 32}, {256, 16}, {256, 8}, {128, 64}, {128, 32}, {128, 16}};
+            return {{256, 64}, {256, 16}, {256, 8}, {128, 32}, {128, 16}};
+        case AGIS_KNOB_SRC_BATCH:
+            if (mixed) return {};
+            return {{0, 0}, {1, 0}, {2, 0}, {4, 0}, {8, 0}, {16, 0}};
+        case AGIS_KNOB_MIX_SUMS:
+            if (!mixed) return {};
+            return {{4, 16}, {2, 32}, {8, 8}, {4, 8}, {2, 16}, {8, 4}};
+        case AGIS_KNOB_MIX_SOLVE5:
+            if (!mixed) return {};
+            return {{128, 0}, {64, 0}, {256, 0}};
+        case AGIS_KNOB_ATT_ACCUM:
+            if (mixed) return {{0, 0}, {0, 32}, {0, 16}, {0, 8}};
+            return {{0, 0}, {0, 16}, {0, 8}, {0, 4}};
+        default:
+            return {{256, 16}, {256, 8}, {128, 16}, {128, 32}, {256, 4}};
+    }
+}
+}  // namespace
+
 extern "C" {
 
 int agis_abi_version(void) { return AGIS_ABI_VERSION; }
@@ -770,7 +835,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     c->n_sblocks = c->n_sm * 8;
     c->mixed = cfg->precision == 1;
     if (c->mixed) {
-        if ((rc = dalloc(c, &c->ms, n)) || (rc = dalloc(c, &c->mt, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
+        if ((rc = dalloc(c, &c->mo.s, n)) || (rc = dalloc(c, &c->mo.r, n)) || (rc = dalloc(c, &c->mo.ac, n)) ||
+            (rc = dalloc(c, &c->mo.t, n)) || (rc = dalloc(c, &c->d_att, 4 * (size_t)n_coef)) ||
             (rc = dalloc(c, &c->d_cal, n_cal)) || (rc = dalloc(c, &c->mw.scale, n_src)) ||
             (rc = dalloc(c, &c->mw.round, n_src)) || (rc = dalloc(c, &c->mw.fin, n_src)) ||
             (rc = dalloc(c, &c->mw.sums, n_src)))
@@ -1117,7 +1183,7 @@ int agis_get_residuals(agis_ctx* c, double* R_out, double* W_out) {
     if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
     if (!c->tmpW) AGIS_TRY(dalloc(c, &c->tmpW, (size_t)c->n_obs));
     if (c->mixed)
-        launch_mix_rw(c->n_obs, c->perm_in, c->ms, c->tmpR, c->tmpW, c->stream);
+        launch_mix_rw(c->n_obs, c->perm_in, c->mo, c->tmpR, c->tmpW, c->stream);
     else
         k_rec_rw<<<grid_for(c->n_obs, 256), 256, 0, c->stream>>>(c->n_obs, c->perm_in, c->rec, c->tmpR, c->tmpW);
     if (R_out) AGIS_CU(c, cudaMemcpyAsync(R_out, c->tmpR, c->n_obs * 8, cudaMemcpyDefault, c->stream), "copy R");
@@ -1201,6 +1267,120 @@ int agis_set_asi(agis_ctx* c, int32_t stride, double lambda_max) {
     c->asi_stride = stride;
     c->asi_lam_max = lambda_max;
     drop_graphs(c);   // the stride and the clamp are captured in the ASI graph
+    return AGIS_OK;
+}
+
+// --- launch-shape autotuner (ABI functions below) ---------------------------------------
+
+int agis_autotune(agis_ctx* c, int32_t max_iter, int32_t* n_done, agis_tune_entry* out) {
+    if (!c || max_iter < 0) return AGIS_E_INVALID;
+    if (n_done) *n_done = 0;
+    const int mask = c->cfg.block_mask;
+    if (!(mask & 1)) return fail(c, AGIS_E_INVALID, "the autotuner times iterations with the S block");
+    struct KnobState {
+        std::vector<ShapeCand> cand;
+        std::vector<double> ms;
+        size_t next = 0;
+    };
+    KnobState ks[AGIS_N_KNOBS];
+    for (int k = 0; k < AGIS_N_KNOBS; k++) {
+        ks[k].cand = knob_candidates(k, c->mixed);
+        if ((k == AGIS_KNOB_ATT_ACCUM && !(mask & 2)) || (k == AGIS_KNOB_CAL_ACCUM && !(mask & 4)))
+            ks[k].cand.clear();
+        ks[k].ms.assign(ks[k].cand.size(), -1.0);
+    }
+    // the timed blocks and the knobs each one rates, in order: S pass, S solves, A, C
+    const int groups[4][3] = {{AGIS_KNOB_OBS_PASS, -1, -1},
+                              {AGIS_KNOB_SRC_BATCH, AGIS_KNOB_MIX_SUMS, AGIS_KNOB_MIX_SOLVE5},
+                              {AGIS_KNOB_ATT_ACCUM, -1, -1},
+                              {AGIS_KNOB_CAL_ACCUM, -1, -1}};
+    auto open_knob = [&](int g) -> int {
+        for (int j = 0; j < 3; j++) {
+            const int k = groups[g][j];
+            if (k >= 0 && ks[k].next < ks[k].cand.size()) return k;
+        }
+        return -1;
+    };
+    const int saved_graph = c->cfg.use_graph, saved_prop = c->prop_every, saved_asi = c->asi_stride;
+    c->cfg.use_graph = 0;
+    c->prop_every = 0;
+    c->asi_stride = 0;
+    Shapes best = c->sh;
+    int it = 0, rc = AGIS_OK;
+    for (; it < max_iter; it++) {
+        int kk[4];
+        bool any = false;
+        Shapes trial = best;
+        for (int g = 0; g < 4; g++) {
+            kk[g] = open_knob(g);
+            if (kk[g] < 0) continue;
+            any = true;
+            const ShapeCand& sc = ks[kk[g]].cand[ks[kk[g]].next];
+            knob_set(trial, kk[g], sc.a, sc.b);
+        }
+        if (!any) break;
+        c->sh = trial;
+        agis_iter_stats st;
+        rc = agis_iterate(c, 1, &st, nullptr);
+        if (rc != AGIS_OK) break;
+        const double t[4] = {st.s.pass_ms, st.s.elapsed_ms - st.s.pass_ms, st.a.elapsed_ms, st.c.elapsed_ms};
+        const bool valid[4] = {!c->mixed || st.s.full_eval == 0, true, true, true};
+        for (int g = 0; g < 4; g++) {
+            if (kk[g] < 0 || !valid[g] || !(t[g] >= 0.0)) continue;
+            KnobState& k = ks[kk[g]];
+            k.ms[k.next++] = t[g];
+            if (k.next == k.cand.size()) {
+                size_t arg = 0;
+                for (size_t j = 1; j < k.ms.size(); j++)
+                    if (k.ms[j] < k.ms[arg]) arg = j;
+                knob_set(best, kk[g], k.cand[arg].a, k.cand[arg].b);
+            }
+        }
+    }
+    c->sh = best;
+    c->cfg.use_graph = saved_graph;
+    c->prop_every = saved_prop;
+    c->asi_stride = saved_asi;
+    drop_graphs(c);
+    if (n_done) *n_done = it;
+    if (out) {
+        for (int k = 0; k < AGIS_N_KNOBS; k++) {
+            agis_tune_entry& e = out[k];
+            e.knob = k;
+            knob_get(best, k, e.a, e.b);
+            e.n_tried = (int32_t)ks[k].next;
+            e.best_ms = -1.0;
+            for (size_t j = 0; j < ks[k].next; j++)
+                if (e.best_ms < 0.0 || ks[k].ms[j] < e.best_ms) e.best_ms = ks[k].ms[j];
+            e.default_ms = ks[k].next > 0 ? ks[k].ms[0] : -1.0;
+        }
+    }
+    return rc;
+}
+
+int agis_get_tuning(const agis_ctx* c, agis_tune_entry* out) {
+    if (!c || !out) return AGIS_E_INVALID;
+    for (int k = 0; k < AGIS_N_KNOBS; k++) {
+        out[k].knob = k;
+        knob_get(c->sh, k, out[k].a, out[k].b);
+        out[k].n_tried = 0;
+        out[k].best_ms = -1.0;
+        out[k].default_ms = -1.0;
+    }
+    return AGIS_OK;
+}
+
+int agis_set_tuning(agis_ctx* c, const agis_tune_entry* in, int32_t n) {
+    if (!c || n < 0 || (n > 0 && !in)) return AGIS_E_INVALID;
+    Shapes sh = c->sh;
+    for (int32_t i = 0; i < n; i++) {
+        const int k = in[i].knob;
+        if (k < 0 || k >= AGIS_N_KNOBS || !knob_valid(k, in[i].a, in[i].b))
+            return fail(c, AGIS_E_INVALID, "launch shape outside the knob's range");
+        knob_set(sh, k, in[i].a, in[i].b);
+    }
+    c->sh = sh;
+    drop_graphs(c);
     return AGIS_OK;
 }
 

@@ -83,17 +83,20 @@ struct __align__(16) ObsRec {
 };
 static_assert(sizeof(ObsRec) == 64, "record must be 64 bytes");
 
-// Mixed-precision records (source order), two 32-byte halves.  MixS holds what the source
-// solve reads: the residual as an unevaluated float pair R = Rh + Rl (about 48 significant
-// bits, so that every per-observation operation runs on the FP32 pipe), the FP32 design row
-// A = (Ap, Aq, Aw, Ap tau, Aq tau) (Eq. ubardiff), sigma (negative for AC) and the weight.
-// MixT holds what the A and C passes gather besides R and W: the attitude partial g, the
-// descriptor, and the time as knot interval l with the offset u = (t - tau_l) / dt.
-struct __align__(16) MixS {
-    float Rh, Rl;   // residual = Rh + Rl
+// Mixed-precision per-observation arrays (source order).  Every per-observation operation
+// of the mixed form runs on the FP32 pipe; the residual is kept as an unevaluated float pair
+// R = Rh + Rl (about 48 significant bits).
+//   s   what the source solve reads besides R: the FP32 design row A = (Ap, Aq, Aw, Ap tau,
+//       Aq tau) (Eq. ubardiff) and sigma (negative for AC)                     20 B
+//   r   the residual pair (Rh, Rl), in its own array so that the linearized observation
+//       pass reads and writes 8 B of it per observation                        8 B
+//   ac  what the A and C blocks read besides the partials: (W, W Rh) after the source
+//       update; the per-observation path of the S block keeps its round weights in .x    8 B
+//   t   the attitude partial g, the descriptor, and the time as knot interval l with the
+//       offset u = (t - tau_l) / dt                                            32 B
+struct MixS {
     float Ap, Aq, Aw, tau;
     float sig;      // +sigma for AL, -sigma for AC
-    float W;        // w / (sigma^2 + eps^2) after the source update
 };
 struct __align__(16) MixT {
     float g[4];     // dR/dq / ||s||
@@ -102,7 +105,13 @@ struct __align__(16) MixT {
     float u;        // (t - tau_l) / knot interval
     uint32_t pad;
 };
-static_assert(sizeof(MixS) == 32 && sizeof(MixT) == 32, "mixed records must be 32 bytes");
+static_assert(sizeof(MixS) == 20 && sizeof(MixT) == 32, "mixed record sizes");
+struct MixObs {
+    MixS* s;
+    float2* r;
+    float2* ac;
+    MixT* t;
+};
 
 // Per-source state of the mixed S block between its kernels.
 struct __align__(16) SrcScale {
@@ -158,6 +167,18 @@ struct Settings {
     double lambda2;
     int rhs_norm_term;
     double pivot_tol;
+};
+
+// Launch shapes chosen by the autotuner.  Every kernel they shape gives each observation,
+// source, knot interval or calibration parameter to one thread or one warp with the same
+// arithmetic whatever the shape, so the results do not depend on them.
+struct Shapes {
+    int obs_threads = 256, obs_bps = 64;  // observation pass: threads per block, blocks per SM (grid cap)
+    int src_batch = 0;                    // FP64 S solves: sources per work fetch (0: n_src / 2432 in 1..32)
+    int sums_warps = 4, sums_bps = 16;    // mixed S sums and final pass: warps per block, blocks per SM
+    int solve5_threads = 128;             // mixed 5x5 solves: threads per block
+    int att_bps = 0;                      // A accumulation: blocks per SM (0: 32 FP64 form, 64 mixed form)
+    int cal_threads = 256, cal_bps = 16;  // C accumulation: threads per block, blocks per SM
 };
 
 // ---------------------------------------------------------------------------------------

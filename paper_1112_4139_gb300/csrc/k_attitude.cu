@@ -289,10 +289,11 @@ __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ s
 }
 
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
-                      int n_iv, const ObsRec* rec, const double* att, double* blk, cudaStream_t s) {
+                      int n_iv, const ObsRec* rec, const double* att, double* blk, const Shapes& sh, cudaStream_t s) {
     int warps = n_iv;
     int blocks = (warps + 3) / 4;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    const int bps = sh.att_bps > 0 ? sh.att_bps : 32;
+    if (blocks > 152 * bps) blocks = 152 * bps;
     if (blocks < 1) blocks = 1;
     k_att_accum<<<blocks, 128, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
 }

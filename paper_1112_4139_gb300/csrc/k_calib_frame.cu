@@ -16,7 +16,24 @@ __global__ void k_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, cons
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_cal; k += nw) {
         double sw = 0.0, swr = 0.0;
-        for (int64_t j = cal_off[k] + lane; j < cal_off[k + 1]; j += kWarp) {
+        const int64_t end = cal_off[k + 1];
+        int64_t j = cal_off[k] + lane;
+        // four independent gathers in flight per lane; the sums keep the order j, j + 32, ...
+        for (; j + 3 * kWarp < end; j += 4 * kWarp) {
+            const uint32_t p0 = perm_c[j], p1 = perm_c[j + kWarp], p2 = perm_c[j + 2 * kWarp],
+                           p3 = perm_c[j + 3 * kWarp];
+            const double W0 = rec[p0].W, R0 = rec[p0].R, W1 = rec[p1].W, R1 = rec[p1].R;
+            const double W2 = rec[p2].W, R2 = rec[p2].R, W3 = rec[p3].W, R3 = rec[p3].R;
+            sw += W0;
+            swr += W0 * R0;
+            sw += W1;
+            swr += W1 * R1;
+            sw += W2;
+            swr += W2 * R2;
+            sw += W3;
+            swr += W3 * R3;
+        }
+        for (; j < end; j += kWarp) {
             const ObsRec* r = rec + perm_c[j];
             const double W = r->W;
             sw += W;
@@ -62,11 +79,12 @@ __global__ void k_cal_project(int n_days, const double* __restrict__ dtil, doubl
 }
 
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
-                double* dtil, int* rd, double* cal, cudaStream_t s) {
-    int blocks = (n_cal + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+                double* dtil, int* rd, double* cal, const Shapes& sh, cudaStream_t s) {
+    const int wpb = sh.cal_threads / 32;
+    int blocks = (n_cal + wpb - 1) / wpb;
+    if (blocks > 152 * sh.cal_bps) blocks = 152 * sh.cal_bps;
     if (blocks < 1) blocks = 1;
-    k_cal_accum<<<blocks, 256, 0, s>>>(n_cal, perm_c, cal_off, rec, tol, dtil, rd);
+    k_cal_accum<<<blocks, sh.cal_threads, 0, s>>>(n_cal, perm_c, cal_off, rec, tol, dtil, rd);
     k_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal);
 }
 

@@ -152,16 +152,16 @@ __device__ __forceinline__ uint32_t fkey(float x) {
 __device__ __forceinline__ float fkey_inv(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
-__device__ __forceinline__ uint32_t xkey(const MixS* rs, int j) {
-    const float2 v = *reinterpret_cast<const float2*>(&rs[j].sig);
-    return fkey(rs[j].Rh / fabsf(v.x));
+__device__ __forceinline__ uint32_t xkey(const MixS* rs, const float2* rr, int j) {
+    return fkey(rr[j].x / fabsf(rs[j].sig));
 }
 
 // keys of one source: from a shared-memory copy when the source fits, else recomputed
 struct KeySrc {
     const uint32_t* sk;
     const MixS* rs;
-    __device__ __forceinline__ uint32_t operator()(int j) const { return sk ? sk[j] : xkey(rs, j); }
+    const float2* rr;
+    __device__ __forceinline__ uint32_t operator()(int j) const { return sk ? sk[j] : xkey(rs, rr, j); }
 };
 
 // the ka-th and kb-th smallest keys (0-based), by a 4-pass radix select with 8-bit digits in
@@ -251,8 +251,8 @@ __device__ float mix_robust_sigma(const KeySrc& key, int n, int* hist, int lane)
 // Class sums of one source for one round (whole warp), shifted to the previous solution:
 // h' = R - A dp, so that Q(y) = hh - 2 d'Ah + d'AA d is formed without cancellation.  The AL
 // rows of a source come first (rows [0, nal)), the AC rows after them.
-__device__ __forceinline__ void class_sums(const MixS* rs, int n, int nal, int lane, const SrcRound& in, int wfn,
-                                           RoundSums* out) {
+__device__ __forceinline__ void class_sums(const MixS* rs, const float2* rr, int n, int nal, int lane,
+                                           const SrcRound& in, int wfn, RoundSums* out) {
     float* o = reinterpret_cast<float*>(out);
     int cnt = 0;
 #pragma unroll 1
@@ -265,10 +265,11 @@ __device__ __forceinline__ void class_sums(const MixS* rs, int n, int nal, int l
         const int lo = c ? nal : 0, hi = c ? n : nal;
         for (int j = lo + lane; j < hi; j += kWarp) {
             const MixS r = rs[j];
+            const float Rh = rr[j].x;
             float A[5];
             arow(r, A);
-            const float hp = r.Rh - adot(A, in.dp);
-            const float w = round_weight(in, r.Rh, hp, c, wfn);
+            const float hp = Rh - adot(A, in.dp);
+            const float w = round_weight(in, Rh, hp, c, wfn);
             cnt += (w < 0.2f);
 #pragma unroll
             for (int a = 0; a < 5; a++) {
@@ -299,8 +300,9 @@ __device__ __forceinline__ void class_sums(const MixS* rs, int n, int nal, int l
 
 // ---- general path (sigma varies within a class): per-observation sweeps for every
 // excess-noise step, FP32 sums shifted to the previous round's solution.
-__device__ __forceinline__ void gen_normals(MixS* rs, int n, int lane, float y, bool refresh, const float* dp,
-                                            float yp, int wfn, double* N, double* b, int& nout) {
+__device__ __forceinline__ void gen_normals(const MixS* rs, const float2* rr, float2* ac, int n, int lane, float y,
+                                            bool refresh, const float* dp, float yp, int wfn, double* N, double* b,
+                                            int& nout) {
     float Nf[15], bf[5];
 #pragma unroll
     for (int i = 0; i < 15; i++) Nf[i] = 0.0f;
@@ -312,11 +314,11 @@ __device__ __forceinline__ void gen_normals(MixS* rs, int n, int lane, float y, 
         float A[5];
         arow(r, A);
         const float s2 = r.sig * r.sig;
-        const float h = r.Rh - adot(A, dp);
-        float w = r.W;
+        const float h = rr[j].x - adot(A, dp);
+        float w = ac[j].x;
         if (refresh) {
             w = wfun_f(h / sqrtf(s2 + yp), wfn);
-            rs[j].W = w;
+            ac[j].x = w;
         }
         cnt += (w < 0.2f);
         const float W = w / (s2 + y);
@@ -335,16 +337,16 @@ __device__ __forceinline__ void gen_normals(MixS* rs, int n, int lane, float y, 
     nout = warp_sum_int(cnt);
 }
 
-__device__ __forceinline__ void gen_q(const MixS* rs, int n, int lane, const float* dp, const float* dl, float y,
-                                      double& Q, double& S2) {
+__device__ __forceinline__ void gen_q(const MixS* rs, const float2* rr, const float2* ac, int n, int lane,
+                                      const float* dp, const float* dl, float y, double& Q, double& S2) {
     float q = 0.0f, s = 0.0f;
     for (int j = lane; j < n; j += kWarp) {
         const MixS r = rs[j];
         float A[5];
         arow(r, A);
-        const float R = (r.Rh - adot(A, dp)) - adot(A, dl);
+        const float R = (rr[j].x - adot(A, dp)) - adot(A, dl);
         const float den = r.sig * r.sig + y;
-        const float t = r.W * R * R / den;
+        const float t = ac[j].x * R * R / den;
         q += t;
         s += t / den;
     }
@@ -352,17 +354,17 @@ __device__ __forceinline__ void gen_q(const MixS* rs, int n, int lane, const flo
     S2 = (double)warp_sum_f(s);
 }
 
-// R <- R - A d and the chi^2 term, for one record (float-pair arithmetic)
-__device__ __forceinline__ float apply_update(MixS* r, const MixS& v, const float* dh, const float* dl, float W) {
+// R <- R - A d (float-pair arithmetic), the A/C inputs (W, W Rh), and the chi^2 term
+__device__ __forceinline__ float apply_update(const MixS& v, float2 R, const float* dh, const float* dl, float W,
+                                              float2* rr, float2* ac) {
     float A[5];
     arow(v, A);
     float sh, sl;
     row_dot_pair(A, dh, dl, sh, sl);
-    float Rh = v.Rh, Rl = v.Rl;
-    pair_add(Rh, Rl, -sh, -sl);
-    *reinterpret_cast<float4*>(r) = make_float4(Rh, Rl, v.Ap, v.Aq);
-    r->W = W;
-    return W * Rh * Rh;
+    pair_add(R.x, R.y, -sh, -sl);
+    *rr = R;
+    *ac = make_float2(W, W * R.x);
+    return W * R.x * R.x;
 }
 
 __device__ __forceinline__ void write_source(const SrcOutPtrs& out, int i, const double* d, const double* U, double y,
@@ -389,16 +391,14 @@ __device__ __forceinline__ void write_source(const SrcOutPtrs& out, int i, const
     out.rankdef[i] = rd;
 }
 
-__device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n, MixS* rs, double s2min, float vs,
-                                               const SrcOutPtrs& out, int lane) {
+__device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n, const MixS* rs, float2* rr,
+                                               float2* ac, double s2min, float vs, const SrcOutPtrs& out, int lane) {
     const double tol_piv = fmax(st.pivot_tol, kMixPivotTol);
     if (st.robust) {
-        for (int j = lane; j < n; j += kWarp) {
-            const MixS r = rs[j];
-            rs[j].W = vs > 0.0f ? wfun_f((r.Rh / fabsf(r.sig)) / vs, st.weight_fn) : 1.0f;
-        }
+        for (int j = lane; j < n; j += kWarp)
+            ac[j].x = vs > 0.0f ? wfun_f((rr[j].x / fabsf(rs[j].sig)) / vs, st.weight_fn) : 1.0f;
     } else {
-        for (int j = lane; j < n; j += kWarp) rs[j].W = 1.0f;
+        for (int j = lane; j < n; j += kWarp) ac[j].x = 1.0f;
     }
     __syncwarp();
     double d[5] = {0, 0, 0, 0, 0};
@@ -411,23 +411,23 @@ __device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n,
         const float yp = (float)y;
         double N[15], b[5], dl[5];
         y = 0.0;
-        gen_normals(rs, n, lane, 0.0f, rnd > 0, dpf, yp, st.weight_fn, N, b, nout);
+        gen_normals(rs, rr, ac, n, lane, 0.0f, rnd > 0, dpf, yp, st.weight_fn, N, b, nout);
         nu = n - nout - 5;
         rd = chol5(N, U, tol_piv);
         chol5_solve(U, b, dl);
         float dlf[5] = {(float)dl[0], (float)dl[1], (float)dl[2], (float)dl[3], (float)dl[4]};
-        gen_q(rs, n, lane, dpf, dlf, 0.0f, Q, S2);
+        gen_q(rs, rr, ac, n, lane, dpf, dlf, 0.0f, Q, S2);
         Q0 = Q;
         if (st.robust && nu > 0 && Q0 > (double)nu) {
             const double tol = 1e-12 * s2min;
             for (int it = 0; it < st.n_eps; it++) {
                 const double dy = (1.0 - Q / (double)nu) * Q / (-S2);
                 y = fmax(0.0, y + dy);
-                gen_normals(rs, n, lane, (float)y, false, dpf, yp, st.weight_fn, N, b, nout);
+                gen_normals(rs, rr, ac, n, lane, (float)y, false, dpf, yp, st.weight_fn, N, b, nout);
                 rd = chol5(N, U, tol_piv);
                 chol5_solve(U, b, dl);
                 for (int a = 0; a < 5; a++) dlf[a] = (float)dl[a];
-                gen_q(rs, n, lane, dpf, dlf, (float)y, Q, S2);
+                gen_q(rs, rr, ac, n, lane, dpf, dlf, (float)y, Q, S2);
                 if (fabs(dy) <= tol) break;
             }
         }
@@ -439,7 +439,7 @@ __device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n,
     float chi = 0.0f;
     for (int j = lane; j < n; j += kWarp) {
         const MixS v = rs[j];
-        chi += apply_update(rs + j, v, dh, dlo, v.W / (v.sig * v.sig + (float)y));
+        chi += apply_update(v, rr[j], dh, dlo, ac[j].x / (v.sig * v.sig + (float)y), rr + j, ac + j);
     }
     const double chid = warp_sum((double)chi);
     if (lane == 0) {
@@ -460,8 +460,7 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
                                                      const float* __restrict__ sigma, const double* __restrict__ mu,
                                                      const int32_t* __restrict__ obs_src,
                                                      const double* __restrict__ geo, const double* __restrict__ att,
-                                                     const double* __restrict__ cal, MixS* __restrict__ ms,
-                                                     MixT* __restrict__ mt) {
+                                                     const double* __restrict__ cal, MixObs mo) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
         const double* gp = geo + 16 * (size_t)obs_src[o];
         SrcGeo S;
@@ -472,26 +471,27 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
         ObsOut ob;
         observe<true>(G, S, t, m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
         MixS a;
-        split_pair(ob.R, a.Rh, a.Rl);
+        float2 R;
+        split_pair(ob.R, R.x, R.y);
         a.Ap = (float)ob.A[0];
         a.Aq = (float)ob.A[1];
         a.Aw = (float)ob.A[2];
         a.tau = (float)ob.tau;
         a.sig = meta_kind(m) ? -sigma[o] : sigma[o];
-        a.W = 0.0f;
-        ms[o] = a;
+        mo.s[o] = a;
+        mo.r[o] = R;
         MixT b;
         for (int k = 0; k < 4; k++) b.g[k] = (float)ob.g[k];
         b.meta = m;
         b.l = left_index(G, t);
         b.u = (float)((double)(t - knot_at(G, b.l)) * G.inv_knot_dt);
         b.pad = 0;
-        mt[o] = b;
+        mo.t[o] = b;
     }
 }
 
 // R += sum_j B_j g . d_a[l-3+j] + d_c[k]  (dR/da_n = g B_n, dR/dc_k = 1; Eqs. dfadq, pdC)
-__global__ void __launch_bounds__(256) k_mix_correct(DevGeo G, int64_t n_obs, MixS* __restrict__ ms,
+__global__ void __launch_bounds__(256) k_mix_correct(DevGeo G, int64_t n_obs, float2* __restrict__ mr,
                                                      const MixT* __restrict__ mt, const float4* __restrict__ d_att,
                                                      const float2* __restrict__ d_cal) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
@@ -506,10 +506,10 @@ __global__ void __launch_bounds__(256) k_mix_correct(DevGeo G, int64_t n_obs, Mi
             corr = fmaf(B[j], r.g[0] * v.x + r.g[1] * v.y + r.g[2] * v.z + r.g[3] * v.w, corr);
         }
         const float2 dc = __ldg(d_cal + meta_cal(r.meta));
-        float2 R = *reinterpret_cast<const float2*>(ms + o);
+        float2 R = mr[o];
         pair_add(R.x, R.y, dc.x, dc.y);
         pair_add(R.x, R.y, corr, 0.0f);
-        *reinterpret_cast<float2*>(ms + o) = R;
+        mr[o] = R;
     }
 }
 
@@ -523,8 +523,7 @@ constexpr int kKeyCap = 1536;  // keys of a source kept in shared memory (6 KB p
 __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st, const int64_t* __restrict__ src_off,
                                                                      const int32_t* __restrict__ src_nal,
                                                                      const int32_t* __restrict__ src_order,
-                                                                     int32_t n_src, const MixS* __restrict__ ms,
-                                                                     MixSrcWork w) {
+                                                                     int32_t n_src, MixObs mo, MixSrcWork w) {
     __shared__ int hist_all[kScaleWarps][512];
     __shared__ uint32_t keys_all[kScaleWarps][kKeyCap];
     const int lane = threadIdx.x & 31;
@@ -546,13 +545,13 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
             }
             continue;
         }
-        const MixS* rs = ms + o0;
+        const MixS* rs = mo.s + o0;
+        const float2* rr = mo.r + o0;
         const bool in_smem = n <= kKeyCap;
         float lo[2] = {3.0e38f, 3.0e38f}, hi[2] = {0.0f, 0.0f};
         for (int j = lane; j < n; j += kWarp) {
-            const float2 v = *reinterpret_cast<const float2*>(&rs[j].sig);
-            const float sg = v.x;
-            if (in_smem) skeys[j] = fkey(rs[j].Rh / fabsf(sg));
+            const float sg = rs[j].sig;
+            if (in_smem) skeys[j] = fkey(rr[j].x / fabsf(sg));
             if (sg < 0.0f) {
                 lo[1] = fminf(lo[1], -sg);
                 hi[1] = fmaxf(hi[1], -sg);
@@ -571,7 +570,7 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
         __syncwarp();
         const bool has0 = hi[0] > 0.0f, has1 = hi[1] > 0.0f;
         const bool uni = (!has0 || lo[0] == hi[0]) && (!has1 || lo[1] == hi[1]);
-        const KeySrc key{in_smem ? skeys : nullptr, rs};
+        const KeySrc key{in_smem ? skeys : nullptr, rs, rr};
         SrcRound in;
         for (int a = 0; a < 5; a++) in.dp[a] = 0.0f;
         in.isd[0] = in.isd[1] = 0.0f;
@@ -591,33 +590,34 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
             w.scale[i] = sc;
             w.round[i] = in;
         }
-        if (uni) class_sums(rs, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
+        if (uni) class_sums(rs, rr, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
         __syncwarp();
     }
 }
 
 // class sums of round r >= 1 (weights and shift from the previous round's solution)
 constexpr int kSumWarps = 4;
-__global__ void __launch_bounds__(32 * kSumWarps) k_mix_sums(Settings st, const int64_t* __restrict__ src_off,
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) k_mix_sums(Settings st, const int64_t* __restrict__ src_off,
                                                              const int32_t* __restrict__ src_nal,
                                                              const int32_t* __restrict__ src_order, int32_t n_src,
-                                                             const MixS* __restrict__ ms, MixSrcWork w) {
+                                                             MixObs mo, MixSrcWork w) {
     const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * kSumWarps;
-    for (int q = blockIdx.x * kSumWarps + (threadIdx.x >> 5); q < n_src; q += nw) {
+    const int nw = gridDim.x * kW;
+    for (int q = blockIdx.x * kW + (threadIdx.x >> 5); q < n_src; q += nw) {
         const int i = src_order[q];
         if (w.scale[i].flags != 1) continue;
         const int64_t o0 = src_off[i];
         const int n = (int)(src_off[i + 1] - o0);
         const SrcRound in = w.round[i];
-        class_sums(ms + o0, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
+        class_sums(mo.s + o0, mo.r + o0, n, src_nal[i], lane, in, st.weight_fn, w.sums + i);
     }
 }
 
 // the 5x5 algebra of one round, one thread per source: N(y), b(y), Q(y) from the class sums,
 // y = 0 first, then the rational steps of the excess variance; d = d_prev + delta.  Writes the
 // FP32 inputs of the next round, or after the last round the final update and the outputs.
-__global__ void __launch_bounds__(128) k_mix_solve5(Settings st, int last, const int64_t* __restrict__ src_off,
+__global__ void __launch_bounds__(256) k_mix_solve5(Settings st, int last, const int64_t* __restrict__ src_off,
                                                     int32_t n_src, SrcOutPtrs out, MixSrcWork w) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_src) return;
@@ -675,27 +675,31 @@ __global__ void __launch_bounds__(128) k_mix_solve5(Settings st, int last, const
 }
 
 // R <- R - A d (float pairs), W = w / (sigma_c^2 + eps^2) with the last round's weights, chi^2
-__global__ void __launch_bounds__(32 * kSumWarps) k_mix_final(Settings st, const int64_t* __restrict__ src_off,
+template <int kW>
+__global__ void __launch_bounds__(32 * kW) k_mix_final(Settings st, const int64_t* __restrict__ src_off,
                                                               const int32_t* __restrict__ src_order, int32_t n_src,
-                                                              SrcOutPtrs out, MixS* __restrict__ ms, MixSrcWork w) {
+                                                              SrcOutPtrs out, MixObs mo, MixSrcWork w) {
     const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * kSumWarps;
-    for (int q = blockIdx.x * kSumWarps + (threadIdx.x >> 5); q < n_src; q += nw) {
+    const int nw = gridDim.x * kW;
+    for (int q = blockIdx.x * kW + (threadIdx.x >> 5); q < n_src; q += nw) {
         const int i = src_order[q];
         if (w.scale[i].flags != 1) continue;
         const int64_t o0 = src_off[i];
         const int n = (int)(src_off[i + 1] - o0);
         const SrcRound in = w.round[i];
         const SrcFinal f = w.fin[i];
-        MixS* rs = ms + o0;
+        const MixS* rs = mo.s + o0;
+        float2* rr = mo.r + o0;
+        float2* ac = mo.ac + o0;
         float chi = 0.0f;
         for (int j = lane; j < n; j += kWarp) {
             const MixS v = rs[j];
+            const float2 R = rr[j];
             float A[5];
             arow(v, A);
             const int cls = v.sig < 0.0f ? 1 : 0;
-            const float wgt = round_weight(in, v.Rh, v.Rh - adot(A, in.dp), cls, st.weight_fn);
-            chi += apply_update(rs + j, v, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]));
+            const float wgt = round_weight(in, R.x, R.x - adot(A, in.dp), cls, st.weight_fn);
+            chi += apply_update(v, R, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]), rr + j, ac + j);
         }
         chi = warp_sum_f(chi);
         if (lane == 0) {
@@ -706,7 +710,7 @@ __global__ void __launch_bounds__(32 * kSumWarps) k_mix_final(Settings st, const
 }
 
 __global__ void __launch_bounds__(32 * kSumWarps) k_mix_general(Settings st, const int64_t* __restrict__ src_off,
-                                                                int32_t n_src, SrcOutPtrs out, MixS* __restrict__ ms,
+                                                                int32_t n_src, SrcOutPtrs out, MixObs mo,
                                                                 MixSrcWork w) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSumWarps;
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(32 * kSumWarps) k_mix_general(Settings st, con
         if (sc.flags != 0) continue;
         const int64_t o0 = src_off[i];
         const int n = (int)(src_off[i + 1] - o0);
-        mix_solve_general(st, i, n, ms + o0, sc.s2min, sc.vs, out, lane);
+        mix_solve_general(st, i, n, mo.s + o0, mo.r + o0, mo.ac + o0, sc.s2min, sc.vs, out, lane);
     }
 }
 
@@ -731,6 +735,36 @@ __global__ void __launch_bounds__(32 * kSumWarps) k_mix_general(Settings st, con
 constexpr int kAccVals = 116;
 constexpr int kAccPad = 117;
 constexpr int kAttWarps = 2;
+// Observations in flight per lane: the records of the next kAttStages observations of a lane
+// are copied into shared memory by cp.async while the current one is summed, and the
+// time-order indices one round further ahead are held in registers, so that neither the
+// index nor the record gather waits on the arithmetic (the kernel holds 116 accumulators per
+// lane and runs at 8 warps per SM, too few to hide a dependent gather by occupancy).
+constexpr int kAttStages = 4;
+struct __align__(16) AttStage {
+    MixT t;
+    float2 ac;
+    float2 pad;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void att_stage_load(AttStage* st, const MixT* mt, const float2* mac, uint32_t o) {
+    cp_async16(&st->t, mt + o);
+    cp_async16(reinterpret_cast<char*>(&st->t) + 16, reinterpret_cast<const char*>(mt + o) + 16);
+    cp_async8(&st->ac, mac + o);
+}
 
 __host__ __device__ constexpr int mtri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
 __host__ __device__ constexpr int mtri16(int i, int j) { return i * 16 - i * (i - 1) / 2 + (j - i); }
@@ -739,11 +773,12 @@ static_assert(mtri16(15, 15) == 135 && mtri16(1, 1) == 16, "upper-triangle index
 __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, float lambda2, int rhs_norm,
                                                                   const uint32_t* __restrict__ perm_t,
                                                                   const int64_t* __restrict__ ivl_off, int n_iv,
-                                                                  const MixS* __restrict__ ms,
+                                                                  const float2* __restrict__ mac,
                                                                   const MixT* __restrict__ mt,
                                                                   const double* __restrict__ att,
                                                                   double* __restrict__ blk) {
     __shared__ float red_all[kAttWarps][kWarp * kAccPad];
+    __shared__ AttStage stage_all[kAttWarps][kAttStages][kWarp];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     float* red = red_all[wib];
@@ -780,16 +815,44 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
 #pragma unroll
         for (int k = 0; k < kAccVals; k++) acc[k] = 0.0f;
         const int64_t beg = ivl_off[iv], end = ivl_off[iv + 1];
-        for (int64_t j = beg + lane; j < end; j += kWarp) {
-            const uint32_t o = perm_t[j];
-            const MixT rt = mt[o];
-            const float2 RW = make_float2(ms[o].Rh, ms[o].W);
+        // prologue: the first kAttStages observations of this lane into the stages, and the
+        // indices of the next kAttStages into registers
+        uint32_t pnext[kAttStages];
+#pragma unroll
+        for (int q = 0; q < kAttStages; q++) {
+            const int64_t j = beg + lane + kWarp * q;
+            if (j < end) att_stage_load(&stage_all[wib][q][lane], mt, mac, perm_t[j]);
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int q = 0; q < kAttStages; q++) {
+            const int64_t j = beg + lane + kWarp * (q + kAttStages);
+            pnext[q] = j < end ? perm_t[j] : 0u;
+        }
+        for (int64_t base = beg; base < end; base += kWarp * kAttStages) {
+#pragma unroll
+          for (int q = 0; q < kAttStages; q++) {
+            const int64_t j = base + kWarp * q + lane;
+            cp_async_wait<kAttStages - 1>();  // the oldest outstanding group: this stage
+            AttStage& sg = stage_all[wib][q][lane];
+            const MixT rt = sg.t;
+            const float2 WR = sg.ac;          // (W, W R)
+            __syncwarp();
+            // refill the stage with this lane's observation kAttStages rounds ahead
+            const int64_t jn = j + kWarp * kAttStages;
+            if (jn < end) {
+                att_stage_load(&sg, mt, mac, pnext[q]);
+                const int64_t jf = jn + kWarp * kAttStages;
+                pnext[q] = jf < end ? perm_t[jf] : 0u;
+            }
+            cp_async_commit();
+            if (j >= end) continue;
             float B[4];
             bspline4_lu(G, l, rt.u, B);
             float s[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
-            const float W = RW.y;
+            const float W = WR.x;
             float M[10], r[4], BB[10];
 #pragma unroll
             for (int c = 0; c < 4; c++)
@@ -802,9 +865,8 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
             if (rhs_norm) D = 1.0f - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                float v = RW.x * rt.g[c];
-                if (rhs_norm) v -= 2.0f * lambda2 * D * s[c];
-                r[c] = W * v;
+                r[c] = WR.y * rt.g[c];
+                if (rhs_norm) r[c] -= W * (2.0f * lambda2 * D * s[c]);
             }
 #pragma unroll
             for (int p = 0; p < 10; p++)
@@ -814,7 +876,9 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
             for (int b = 0; b < 4; b++)
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[100 + 4 * b + c] = fmaf(B[b], r[c], acc[100 + 4 * b + c]);
+          }
         }
+        cp_async_wait<0>();
         // compensated cross-lane reduction through shared memory
 #pragma unroll
         for (int k = 0; k < kAccVals; k++) red[lane * kAccPad + k] = acc[k];
@@ -838,16 +902,31 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
 // C block sums from the records (calibration order): N_kk = sum W, b_k = -sum W R; the 1x1
 // robust solve gives d~_k = (b / sqrt(N)) / sqrt(N), or 0 with a rank defect.
 __global__ void k_mix_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, const int64_t* __restrict__ cal_off,
-                                const MixS* __restrict__ ms, double* __restrict__ dtil, int* __restrict__ rd) {
+                                const float2* __restrict__ mac, double* __restrict__ dtil, int* __restrict__ rd) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_cal; k += nw) {
         float sw = 0.0f, swr = 0.0f;
-        for (int64_t j = cal_off[k] + lane; j < cal_off[k + 1]; j += kWarp) {
-            const MixS* r = ms + perm_c[j];
-            const float W = r->W;
-            sw += W;
-            swr = fmaf(W, r->Rh, swr);
+        const int64_t end = cal_off[k + 1];
+        int64_t j = cal_off[k] + lane;
+        // four independent gathers in flight per lane; the sums keep the order j, j + 32, ...
+        for (; j + 3 * kWarp < end; j += 4 * kWarp) {
+            const uint32_t p0 = perm_c[j], p1 = perm_c[j + kWarp], p2 = perm_c[j + 2 * kWarp],
+                           p3 = perm_c[j + 3 * kWarp];
+            const float2 a0 = mac[p0], a1 = mac[p1], a2 = mac[p2], a3 = mac[p3];   // (W, W R)
+            sw += a0.x;
+            swr += a0.y;
+            sw += a1.x;
+            swr += a1.y;
+            sw += a2.x;
+            swr += a2.y;
+            sw += a3.x;
+            swr += a3.y;
+        }
+        for (; j < end; j += kWarp) {
+            const float2 a = mac[perm_c[j]];
+            sw += a.x;
+            swr += a.y;
         }
         const double swd = warp_sum((double)sw);
         const double swrd = warp_sum((double)swr);
@@ -893,7 +972,7 @@ __global__ void k_mix_cal_project(int n_days, const double* __restrict__ dtil, d
 }
 
 // R <- R - A c for a learned proposal c added to the sources (float-pair arithmetic)
-__global__ void k_mix_prop(int32_t n_src, const int64_t* __restrict__ src_off, MixS* __restrict__ ms,
+__global__ void k_mix_prop(int32_t n_src, const int64_t* __restrict__ src_off, MixObs mo,
                            const double* __restrict__ corr) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -901,23 +980,25 @@ __global__ void k_mix_prop(int32_t n_src, const int64_t* __restrict__ src_off, M
         float ch[5], cl[5];
         for (int a = 0; a < 5; a++) split_pair(corr[5 * (size_t)i + a], ch[a], cl[a]);
         for (int64_t o = src_off[i] + lane; o < src_off[i + 1]; o += kWarp) {
-            const MixS v = ms[o];
+            const MixS v = mo.s[o];
             float A[5];
             arow(v, A);
             float sh, sl;
             row_dot_pair(A, ch, cl, sh, sl);
-            float Rh = v.Rh, Rl = v.Rl;
-            pair_add(Rh, Rl, -sh, -sl);
-            *reinterpret_cast<float2*>(ms + o) = make_float2(Rh, Rl);
+            float2 R = mo.r[o];
+            pair_add(R.x, R.y, -sh, -sl);
+            mo.r[o] = R;
+            const float W = mo.ac[o].x;
+            mo.ac[o] = make_float2(W, W * R.x);
         }
     }
 }
 
-__global__ void k_mix_rw(int64_t n, const uint32_t* __restrict__ perm, const MixS* __restrict__ ms,
-                         double* __restrict__ R, double* __restrict__ W) {
+__global__ void k_mix_rw(int64_t n, const uint32_t* __restrict__ perm, const float2* __restrict__ mr,
+                         const float2* __restrict__ mac, double* __restrict__ R, double* __restrict__ W) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-        if (R) R[perm[o]] = (double)ms[o].Rh + (double)ms[o].Rl;
-        if (W) W[perm[o]] = (double)ms[o].W;
+        if (R) R[perm[o]] = (double)mr[o].x + (double)mr[o].y;
+        if (W) W[perm[o]] = (double)mac[o].x;
     }
 }
 
@@ -928,14 +1009,14 @@ __global__ void k_mix_rw(int64_t n, const uint32_t* __restrict__ perm, const Mix
 // correction by the A and C updates since the last source update; both leave d_att, d_cal zero
 void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
-                     const double* att, const double* cal, MixS* ms, MixT* mt, double* geo, float* d_att,
-                     float2* d_cal, int n_coef, int n_cal, cudaStream_t s) {
+                     const double* att, const double* cal, const MixObs& mo, double* geo, float* d_att,
+                     float2* d_cal, int n_coef, int n_cal, const Shapes& sh, cudaStream_t s) {
     if (refresh) {
         launch_src_geo(n_src, src, geo, s);
         k_mix_forward<<<grid_of(n_obs, 256, 152 * 64), 256, 0, s>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo,
-                                                                     att, cal, ms, mt);
+                                                                     att, cal, mo);
     } else {
-        k_mix_correct<<<grid_of(n_obs, 256, 152 * 64), 256, 0, s>>>(G, n_obs, ms, mt,
+        k_mix_correct<<<grid_of(n_obs, sh.obs_threads, 152 * sh.obs_bps), sh.obs_threads, 0, s>>>(G, n_obs, mo.r, mo.t,
                                                                      reinterpret_cast<const float4*>(d_att), d_cal);
     }
     cudaMemsetAsync(d_att, 0, sizeof(float) * 4 * (size_t)n_coef, s);
@@ -943,39 +1024,51 @@ void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const u
 }
 
 void launch_mix_solve(const Settings& st, const int64_t* src_off, const int32_t* src_nal, const int32_t* src_order,
-                      int32_t n_src, const SrcOutPtrs& out, MixS* ms, const MixSrcWork& w, cudaStream_t s) {
+                      int32_t n_src, const SrcOutPtrs& out, const MixObs& mo, const MixSrcWork& w,
+                      const Shapes& sh, cudaStream_t s) {
     const int rounds = st.robust ? st.n_rounds + 1 : 1;
-    const int warp_blocks = grid_of(n_src, kSumWarps, 152 * 16);
-    const int thread_blocks = (n_src + 127) / 128 > 0 ? (n_src + 127) / 128 : 1;
+    const int W = sh.sums_warps;
+    const int warp_blocks = grid_of(n_src, W, 152 * sh.sums_bps);
+    const int t5 = sh.solve5_threads;
+    const int thread_blocks = (n_src + t5 - 1) / t5 > 0 ? (n_src + t5 - 1) / t5 : 1;
     k_mix_scale_sums<<<grid_of(n_src, kScaleWarps, 152 * 8), 32 * kScaleWarps, 0, s>>>(st, src_off, src_nal,
-                                                                                       src_order, n_src, ms, w);
+                                                                                       src_order, n_src, mo, w);
+    auto sums = [&]() {
+        if (W == 2) k_mix_sums<2><<<warp_blocks, 64, 0, s>>>(st, src_off, src_nal, src_order, n_src, mo, w);
+        else if (W == 8) k_mix_sums<8><<<warp_blocks, 256, 0, s>>>(st, src_off, src_nal, src_order, n_src, mo, w);
+        else k_mix_sums<4><<<warp_blocks, 128, 0, s>>>(st, src_off, src_nal, src_order, n_src, mo, w);
+    };
     for (int r = 0; r < rounds; r++) {
-        if (r > 0) k_mix_sums<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_nal, src_order, n_src, ms, w);
-        k_mix_solve5<<<thread_blocks, 128, 0, s>>>(st, r == rounds - 1, src_off, n_src, out, w);
+        if (r > 0) sums();
+        k_mix_solve5<<<thread_blocks, t5, 0, s>>>(st, r == rounds - 1, src_off, n_src, out, w);
     }
-    k_mix_final<<<warp_blocks, 32 * kSumWarps, 0, s>>>(st, src_off, src_order, n_src, out, ms, w);
-    k_mix_general<<<grid_of(n_src, kSumWarps, 152 * 4), 32 * kSumWarps, 0, s>>>(st, src_off, n_src, out, ms, w);
+    if (W == 2) k_mix_final<2><<<warp_blocks, 64, 0, s>>>(st, src_off, src_order, n_src, out, mo, w);
+    else if (W == 8) k_mix_final<8><<<warp_blocks, 256, 0, s>>>(st, src_off, src_order, n_src, out, mo, w);
+    else k_mix_final<4><<<warp_blocks, 128, 0, s>>>(st, src_off, src_order, n_src, out, mo, w);
+    k_mix_general<<<grid_of(n_src, kSumWarps, 152 * 4), 32 * kSumWarps, 0, s>>>(st, src_off, n_src, out, mo, w);
 }
 
 void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t,
-                          const int64_t* ivl_off, int n_iv, const MixS* ms, const MixT* mt, const double* att,
-                          double* blk, cudaStream_t s) {
-    k_mix_att_accum<<<grid_of(n_iv, kAttWarps, 152 * 64), 32 * kAttWarps, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t,
-                                                                                 ivl_off, n_iv, ms, mt, att, blk);
+                          const int64_t* ivl_off, int n_iv, const MixObs& mo, const double* att, double* blk,
+                          const Shapes& sh, cudaStream_t s) {
+    const int bps = sh.att_bps > 0 ? sh.att_bps : 64;
+    k_mix_att_accum<<<grid_of(n_iv, kAttWarps, 152 * bps), 32 * kAttWarps, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t,
+                                                                                 ivl_off, n_iv, mo.ac, mo.t, att, blk);
 }
 
-void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixS* ms,
-                    double* dtil, int* rd, double* cal, float2* d_cal, cudaStream_t s) {
-    k_mix_cal_accum<<<grid_of(n_cal, 8, 152 * 16), 256, 0, s>>>(n_cal, perm_c, cal_off, ms, dtil, rd);
+void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const MixObs& mo,
+                    double* dtil, int* rd, double* cal, float2* d_cal, const Shapes& sh, cudaStream_t s) {
+    k_mix_cal_accum<<<grid_of(n_cal, sh.cal_threads / 32, 152 * sh.cal_bps), sh.cal_threads, 0, s>>>(
+        n_cal, perm_c, cal_off, mo.ac, dtil, rd);
     k_mix_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal, d_cal);
 }
 
-void launch_mix_prop(int32_t n_src, const int64_t* src_off, MixS* ms, const double* corr, cudaStream_t s) {
-    k_mix_prop<<<grid_of(n_src, 8, 152 * 16), 256, 0, s>>>(n_src, src_off, ms, corr);
+void launch_mix_prop(int32_t n_src, const int64_t* src_off, const MixObs& mo, const double* corr, cudaStream_t s) {
+    k_mix_prop<<<grid_of(n_src, 8, 152 * 16), 256, 0, s>>>(n_src, src_off, mo, corr);
 }
 
-void launch_mix_rw(int64_t n, const uint32_t* perm, const MixS* ms, double* R, double* W, cudaStream_t s) {
-    k_mix_rw<<<grid_of(n, 256, 152 * 32), 256, 0, s>>>(n, perm, ms, R, W);
+void launch_mix_rw(int64_t n, const uint32_t* perm, const MixObs& mo, double* R, double* W, cudaStream_t s) {
+    k_mix_rw<<<grid_of(n, 256, 152 * 32), 256, 0, s>>>(n, perm, mo.r, mo.ac, R, W);
 }
 
 }  // namespace agis

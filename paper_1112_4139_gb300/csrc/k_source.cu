@@ -569,22 +569,25 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
 void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
-                     cudaStream_t stream) {
+                     const Shapes& sh, cudaStream_t stream) {
     k_src_geo<<<(n_src + 255) / 256 > 0 ? (n_src + 255) / 256 : 1, 256, 0, stream>>>(n_src, src, geo);
-    int fb = (int)((n_obs + 255) / 256);
-    if (fb > 152 * 64) fb = 152 * 64;
+    const int th = sh.obs_threads;
+    int64_t fb = (n_obs + th - 1) / th;
+    if (fb > 152 * (int64_t)sh.obs_bps) fb = 152 * (int64_t)sh.obs_bps;
     if (fb < 1) fb = 1;
-    k_obs_forward<<<fb, 256, 0, stream>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
+    k_obs_forward<<<(int)fb, th, 0, stream>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
 }
 
 // the per-source solves of the S block on the scratch rows of the observation pass
 void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
                          const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
-                         int* work_counter, int n_blocks, cudaStream_t stream) {
+                         int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream) {
     cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
-    // batch size: 32 sources per warp when there are enough sources to keep ~16 warps per SM busy
+    // batch size: 32 sources per warp when there are enough sources to keep ~16 warps per SM
+    // busy, unless the autotuner chose one
     int batch = n_src / (152 * 16);
     batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
+    if (sh.src_batch > 0) batch = sh.src_batch;
     int warps = (n_src + batch - 1) / batch;
     int blocks = (warps + kSolveWarps - 1) / kSolveWarps;
     if (blocks > n_blocks * 4) blocks = n_blocks * 4;

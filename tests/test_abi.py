@@ -24,11 +24,12 @@ def test_library_builds_and_exports_all_declared_symbols():
     assert declared == set(agis.EXPORTS)
     for name in declared:
         assert hasattr(lib, name), name
-    assert lib.agis_abi_version() == agis.ABI_VERSION == 4
+    assert lib.agis_abi_version() == agis.ABI_VERSION == 5
 
 
 def test_default_config_and_struct_sizes():
     assert C.sizeof(agis.BlockStats) == 104 and C.sizeof(agis.IterStats) == 3 * 104 + 80
+    assert C.sizeof(agis.TuneEntry) == 32
     cfg = agis.default_config()
     assert cfg.precision == 0 and cfg.refresh_every == 8
     assert cfg.robust == 1 and cfg.n_rounds == 4 and cfg.n_eps == 3 and abs(cfg.lambda_att - 1e-3) < 1e-18
