@@ -305,6 +305,7 @@ __device__ __forceinline__ double atan2_small(double y, double x) {
 struct SrcGeo {
     double p[3], q[3], r[3];
     double par, pma, pmd, cosd;
+    float pf[3], qf[3];   // p, q rounded to FP32 (the mixed form's FP32 partials)
 };
 
 __device__ __forceinline__ void source_geo(const double* s5, SrcGeo& S) {
@@ -323,7 +324,18 @@ struct ObsOut {
     double A[5];    // -dR/ds'
     double g[4];    // dR/dq / ||s||
     double tau;     // proper-motion time (years), A[3] = A[0] tau, A[4] = A[1] tau
+    float Af[3];    // FP32 partials (kPartials == 2): A[0..2], g, tau
+    float gf[4];
+    float tauf;
 };
+
+__device__ __forceinline__ float dot3f(const float* a, const float* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void qmulf(const float* a, const float* b, float* c) {
+    c[0] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    c[1] = -a[0] * b[2] + a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    c[2] = a[0] * b[1] - a[1] * b[0] + a[2] * b[3] + a[3] * b[2];
+    c[3] = -a[0] * b[0] - a[1] * b[1] - a[2] * b[2] + a[3] * b[3];
+}
 
 // Residual and partial derivatives of one observation (FP64).
 //   proper direction: Eqs. astro-standard, roemer, classAberr
@@ -334,7 +346,8 @@ struct ObsOut {
 // The field angles depend on the direction only, so neither the aberrated direction nor the
 // attitude quaternion is normalised: the rotation uses |s|^2 R(s/|s|), and the along-scan
 // angle is measured from the field centre after turning by -f Gamma / 2.
-template <bool kPartials>
+// kPartials: 0 residual only, 1 FP64 partials, 2 FP32 partials (Af, gf, tauf)
+template <int kPartials>
 __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_t t, uint32_t meta, double mu,
                                         const double* __restrict__ att, const double* __restrict__ cal,
                                         ObsOut& o) {
@@ -378,7 +391,57 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
         const double zeta0 = -(G.x_fpa[ccd] - (mu - G.mu_c) * G.p_ac - G.x_centre[fov]) / G.F;
         o.R = (zeta0 + c_k) - zeta;
     }
-    if (!kPartials) return;
+    if (kPartials == 0) return;
+    if (kPartials == 2) {
+        // FP32 partials from the FP64 intermediates rounded once (the mixed form keeps its
+        // partials in FP32; their rounding changes the rate of the iteration, not its fixed
+        // point).  Same equations as the FP64 branch below; r = p x q for the normal triad.
+        const float usf[3] = {(float)us[0], (float)us[1], (float)us[2]};
+        const float sf[4] = {(float)s[0], (float)s[1], (float)s[2], (float)s[3]};
+        const float r2 = usf[0] * usf[0] + usf[1] * usf[1];
+        const float ir = rsqrtf(r2);
+        const float cphi = usf[0] * ir, sphi = usf[1] * ir;
+        const float in = rsqrtf(r2 + usf[2] * usf[2]);
+        const float czeta = r2 * ir * in, szeta = usf[2] * in;
+        const bool al = kind == 0;
+        // e = m (AL) or n (AC), and w = the other one (selects, not pointers: registers)
+        const float e[3] = {al ? -sphi : -szeta * cphi, al ? cphi : -szeta * sphi, al ? 0.0f : czeta};
+        const float w3[3] = {al ? -szeta * cphi : -sphi, al ? -szeta * sphi : cphi, al ? czeta : 0.0f};
+        const float x = sf[0], y = sf[1], z = sf[2], w = sf[3];
+        const float xx = x * x, yy = y * y, zz = z * z, ww = w * w;
+        const float Af[9] = {ww + xx - yy - zz,      2.0f * (x * y + z * w), 2.0f * (x * z - y * w),
+                             2.0f * (x * y - z * w), ww - xx + yy - zz,      2.0f * (y * z + x * w),
+                             2.0f * (x * z + y * w), 2.0f * (y * z - x * w), ww - xx - yy + zz};
+        const float ins2 = 1.0f / (xx + yy + zz + ww);
+        const float ec[3] = {(Af[0] * e[0] + Af[3] * e[1] + Af[6] * e[2]) * ins2,
+                             (Af[1] * e[0] + Af[4] * e[1] + Af[7] * e[2]) * ins2,
+                             (Af[2] * e[0] + Af[5] * e[1] + Af[8] * e[2]) * ins2};
+        const float sLf = (float)sL, cLf = (float)cL;
+        const float co = (float)G.cos_obl, so = (float)G.sin_obl, vk = (float)G.vk;
+        const float bf[3] = {cLf, co * sLf, so * sLf};
+        const float vcf[3] = {-vk * sLf, vk * co * cLf, vk * so * cLf};
+        const float ubf[3] = {(float)ub[0], (float)ub[1], (float)ub[2]};
+        const float* pf = S.pf;
+        const float* qf = S.qf;
+        const float rf[3] = {pf[1] * qf[2] - pf[2] * qf[1], pf[2] * qf[0] - pf[0] * qf[2],
+                             pf[0] * qf[1] - pf[1] * qf[0]};
+        const float rbf = dot3f(rf, bf);
+        const float ubv = dot3f(ubf, vcf);
+        const float eub = dot3f(ec, ubf);
+        const float dpar[3] = {-(bf[0] - rf[0] * rbf), -(bf[1] - rf[1] * rbf), -(bf[2] - rf[2] * rbf)};
+        const float secz = 1.0f / czeta;
+        const float sc = (kind == 0) ? secz : 1.0f;
+        o.Af[0] = ((1.0f - ubv) * dot3f(ec, pf) - eub * dot3f(vcf, pf)) * sc;
+        o.Af[1] = ((1.0f - ubv) * dot3f(ec, qf) - eub * dot3f(vcf, qf)) * sc;
+        o.Af[2] = ((1.0f - ubv) * dot3f(ec, dpar) - eub * dot3f(vcf, dpar)) * sc;
+        o.tauf = (float)tau;
+        const float v4[4] = {w3[0], w3[1], w3[2], 0.0f};
+        float gq[4];
+        qmulf(sf, v4, gq);
+        const float k2 = ((kind == 0) ? 2.0f * secz : -2.0f) * ins2;
+        o.gf[0] = gq[0] * k2; o.gf[1] = gq[1] * k2; o.gf[2] = gq[2] * k2; o.gf[3] = gq[3] * k2;
+        return;
+    }
     // m, n in the SRS (Eq. srspqr)
     const double cphi = us[0] * irho, sphi = us[1] * irho;
     double czeta, szeta;

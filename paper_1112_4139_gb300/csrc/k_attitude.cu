@@ -11,43 +11,59 @@ __host__ __device__ constexpr int tri16(int i, int j) { return i * 16 - i * (i -
 __host__ __device__ constexpr int tri4(int i, int j) { return i * 4 - i * (i - 1) / 2 + (j - i); }
 
 constexpr int kStage = 28;  // staged per observation: B[4], M[10], r[4], BB[10]
+constexpr int kAccFP64 = 116;  // distinct products: BB[p] M[m] (10 x 10) and B[b] r[c] (4 x 4)
 
 // One warp per knot interval l (left index), iv = l - 3.  For each observation
 // dR/da = B (x) g and dD/da = -2 B (x) s (Eqs. dfadq, dDldan), so its contribution to the
 // 16x16 block of the interval is W (B B') (x) (g g' + 4 lambda^2 s s') (Eq. normAmod) and
-// to the right-hand side -W B (x) (R g [- 2 lambda^2 D s]).
+// to the right-hand side -W B (x) (R g [- 2 lambda^2 D s]).  The 136 upper entries of the
+// block hold only 100 distinct products (the 10 upper entries of B B' times those of the
+// symmetric 4x4 M), so the lanes accumulate those 100 and the 16 right-hand-side products
+// (4 per lane) and expand them into the 152 outputs at the end.
 __global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int rhs_norm,
                                                    const uint32_t* __restrict__ perm_t,
                                                    const int64_t* __restrict__ ivl_off, int n_iv,
                                                    const ObsRec* __restrict__ rec, const double* __restrict__ att,
                                                    double* __restrict__ blk) {
     __shared__ double stage_all[4][kWarp * kStage];
+    __shared__ double red_all[4][kAccFP64];
+    __shared__ int16_t src_tab[kBlkVals];  // accumulator of each block output
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     double* stg = stage_all[wib];
-    // this lane's outputs: o = lane + 32 k, k = 0..4 (o < 152)
-    int oi[5], oj[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-        int o = lane + 32 * k;
-        oi[k] = -1; oj[k] = -1;
+    double* red = red_all[wib];
+    for (int o = threadIdx.x; o < kBlkVals; o += blockDim.x) {
+        int v;
         if (o < 136) {
             int i = 0;
             while (o >= tri16(i, 15) + 1) i++;
-            oi[k] = i;
-            oj[k] = i + (o - tri16(i, i));
-        } else if (o < kBlkVals) {
-            oi[k] = o - 136;
-            oj[k] = -1;
+            const int jj = i + (o - tri16(i, i));
+            const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
+            v = tri4(bi, bj) * 10 + (ci <= cj ? tri4(ci, cj) : tri4(cj, ci));
+        } else {
+            v = 100 + (o - 136);
         }
+        src_tab[o] = (int16_t)v;
     }
+    __syncthreads();
+    // this lane's accumulators s = lane + 32 k (k < 3: BB[p] M[m]; k = 3: lanes 0-3 BB M,
+    // lanes 4-19 B[b] r[c] of the right-hand side, lanes 20-31 none): the staged factors
+    int fa[4], fb[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int sidx = lane + 32 * k;
+        fa[k] = sidx < 100 ? 18 + sidx / 10 : (sidx < kAccFP64 ? (sidx - 100) >> 2 : 0);
+        fb[k] = sidx < 100 ? 4 + sidx % 10 : 14 + ((sidx - 100) & 3);
+    }
+    const bool k3 = lane < 20;              // accumulator 3 in use
+    const bool k3_rhs = lane >= 4 && k3;    // ... and it is a right-hand-side product
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int iv = blockIdx.x * (blockDim.x >> 5) + wib; iv < n_iv; iv += nwarps) {
         const int l = iv + 3;
         double a[16];
 #pragma unroll
         for (int k = 0; k < 16; k++) a[k] = att[4 * (int64_t)(l - 3) + k];
-        double acc[5] = {0, 0, 0, 0, 0};
+        double acc[4] = {0, 0, 0, 0};
         const int64_t beg = ivl_off[iv], end = ivl_off[iv + 1];
         for (int64_t base = beg; base < end; base += kWarp) {
             const int64_t j = base + lane;
@@ -88,26 +104,21 @@ __global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int
             for (int q = 0; q < cnt; q++) {
                 const double* sq = stg + q * kStage;
 #pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    if (oi[k] < 0) continue;
-                    const int i = oi[k];
-                    if (oj[k] >= 0) {
-                        const int jj = oj[k];
-                        const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
-                        const int mi = ci <= cj ? tri4(ci, cj) : tri4(cj, ci);
-                        acc[k] += sq[18 + tri4(bi, bj)] * sq[4 + mi];
-                    } else {
-                        acc[k] -= sq[i >> 2] * sq[14 + (i & 3)];
-                    }
-                }
+                for (int k = 0; k < 3; k++) acc[k] += sq[fa[k]] * sq[fb[k]];
+                if (k3) acc[3] += sq[fa[3]] * sq[fb[3]];
             }
             __syncwarp();
         }
 #pragma unroll
+        for (int k = 0; k < 3; k++) red[lane + 32 * k] = acc[k];
+        if (k3) red[lane + 96] = k3_rhs ? -acc[3] : acc[3];
+        __syncwarp();
+#pragma unroll
         for (int k = 0; k < 5; k++) {
-            int o = lane + 32 * k;
-            if (o < kBlkVals) blk[(int64_t)iv * kBlkVals + o] = acc[k];
+            const int o = lane + 32 * k;
+            if (o < kBlkVals) blk[(int64_t)iv * kBlkVals + o] = red[src_tab[o]];
         }
+        __syncwarp();
     }
 }
 

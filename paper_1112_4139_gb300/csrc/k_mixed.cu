@@ -466,22 +466,24 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
         SrcGeo S;
         for (int k = 0; k < 3; k++) { S.p[k] = gp[k]; S.q[k] = gp[3 + k]; S.r[k] = gp[6 + k]; }
         S.par = gp[9]; S.pma = gp[10]; S.pmd = gp[11]; S.cosd = gp[12];
+        const float* gf = reinterpret_cast<const float*>(gp + 13);
+        for (int k = 0; k < 3; k++) { S.pf[k] = gf[k]; S.qf[k] = gf[3 + k]; }
         const int64_t t = t_ns[o];
         const uint32_t m = meta[o];
         ObsOut ob;
-        observe<true>(G, S, t, m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
+        observe<2>(G, S, t, m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
         MixS a;
         float2 R;
         split_pair(ob.R, R.x, R.y);
-        a.Ap = (float)ob.A[0];
-        a.Aq = (float)ob.A[1];
-        a.Aw = (float)ob.A[2];
-        a.tau = (float)ob.tau;
+        a.Ap = ob.Af[0];
+        a.Aq = ob.Af[1];
+        a.Aw = ob.Af[2];
+        a.tau = ob.tauf;
         a.sig = meta_kind(m) ? -sigma[o] : sigma[o];
         mo.s[o] = a;
         mo.r[o] = R;
         MixT b;
-        for (int k = 0; k < 4; k++) b.g[k] = (float)ob.g[k];
+        for (int k = 0; k < 4; k++) b.g[k] = ob.gf[k];
         b.meta = m;
         b.l = left_index(G, t);
         b.u = (float)((double)(t - knot_at(G, b.l)) * G.inv_knot_dt);
@@ -770,6 +772,17 @@ __host__ __device__ constexpr int mtri4(int i, int j) { return i * 4 - i * (i - 
 __host__ __device__ constexpr int mtri16(int i, int j) { return i * 16 - i * (i - 1) / 2 + (j - i); }
 static_assert(mtri16(15, 15) == 135 && mtri16(1, 1) == 16, "upper-triangle index of the 16x16 block");
 
+// One knot interval per group of kAttLanes lanes (kWarp / kAttLanes intervals per warp):
+// each lane sums its share of the interval's observations in FP32, and each output of the
+// 16x16 block is then the compensated sum of the group's kAttLanes lane partials.  The
+// attitude normals are nearly singular along the coefficient vector (only the 4 lambda^2
+// norm term, 4e-6 relative, fixes that direction), so the uncompensated per-lane sums must
+// stay short: a whole warp per interval.  With 8 lanes per interval (about 34 observations
+// per lane on 1-h knots) the rounding of the lane sums swamped the norm term and the update
+// along the coefficient vector was lost.
+constexpr int kAttLanes = 32;
+constexpr int kAttGroups = kWarp / kAttLanes;
+
 __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, float lambda2, int rhs_norm,
                                                                   const uint32_t* __restrict__ perm_t,
                                                                   const int64_t* __restrict__ ivl_off, int n_iv,
@@ -779,70 +792,74 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
                                                                   double* __restrict__ blk) {
     __shared__ float red_all[kAttWarps][kWarp * kAccPad];
     __shared__ AttStage stage_all[kAttWarps][kAttStages][kWarp];
+    __shared__ int16_t src_tab[kBlkVals];  // accumulator of each block output (>= 100: right-hand side)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int sub = lane & (kAttLanes - 1);
+    const int grp = lane / kAttLanes;
+    const unsigned gmask = kAttLanes == kWarp ? 0xffffffffu : ((1u << (kAttLanes % kWarp)) - 1u) << (grp * kAttLanes);
     float* red = red_all[wib];
-    // the accumulator index of each of this lane's (up to 5) block outputs o = lane + 32 k
-    int src_idx[5];
-    float sgn[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-        const int o = lane + 32 * k;
-        src_idx[k] = -1;
-        sgn[k] = 1.0f;
+    for (int o = threadIdx.x; o < kBlkVals; o += blockDim.x) {
+        int v;
         if (o < 136) {
             int i = 0;
             while (o >= mtri16(i, 15) + 1) i++;
-            const int j = i + (o - mtri16(i, i));
-            const int bi = i >> 2, ci = i & 3, bj = j >> 2, cj = j & 3;
+            const int jj = i + (o - mtri16(i, i));
+            const int bi = i >> 2, ci = i & 3, bj = jj >> 2, cj = jj & 3;
             const int m = ci <= cj ? mtri4(ci, cj) : mtri4(cj, ci);
-            src_idx[k] = mtri4(bi, bj) * 10 + m;
-        } else if (o < kBlkVals) {
-            src_idx[k] = 100 + (o - 136);
-            sgn[k] = -1.0f;
+            v = mtri4(bi, bj) * 10 + m;
+        } else {
+            v = 100 + (o - 136);
         }
+        src_tab[o] = (int16_t)v;
     }
+    __syncthreads();
     const int nwarps = gridDim.x * kAttWarps;
     const float l4 = 4.0f * lambda2;
-    for (int iv = blockIdx.x * kAttWarps + wib; iv < n_iv; iv += nwarps) {
+    for (int iv0 = (blockIdx.x * kAttWarps + wib) * kAttGroups; iv0 < n_iv; iv0 += nwarps * kAttGroups) {
+        const int iv = iv0 + grp;
+        const bool have = iv < n_iv;
         const int l = iv + 3;
-        // the 16 coefficients of the interval: one conversion per lane, then broadcast
-        const float af = lane < 16 ? (float)att[4 * (int64_t)(l - 3) + lane] : 0.0f;
+        // the 16 coefficients of the interval: two conversions per lane, then broadcast in the group
+        const float af0 = have ? (float)att[4 * (int64_t)(l - 3) + sub] : 0.0f;
+        const float af1 = have ? (float)att[4 * (int64_t)(l - 3) + kAttLanes + sub] : 0.0f;
         float a[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++) a[k] = __shfl_sync(0xffffffffu, af, k);
+        for (int k = 0; k < 16; k++)
+            a[k] = __shfl_sync(0xffffffffu, k < kAttLanes ? af0 : af1, grp * kAttLanes + (k & (kAttLanes - 1)));
         float acc[kAccVals];
 #pragma unroll
         for (int k = 0; k < kAccVals; k++) acc[k] = 0.0f;
-        const int64_t beg = ivl_off[iv], end = ivl_off[iv + 1];
-        // prologue: the first kAttStages observations of this lane into the stages, and the
-        // indices of the next kAttStages into registers
+        const int64_t beg = have ? ivl_off[iv] : 0, end = have ? ivl_off[iv + 1] : 0;
+        // prologue: this lane's first kAttStages observations into the stages, and the indices
+        // of the next kAttStages into registers
         uint32_t pnext[kAttStages];
 #pragma unroll
         for (int q = 0; q < kAttStages; q++) {
-            const int64_t j = beg + lane + kWarp * q;
+            const int64_t j = beg + sub + kAttLanes * q;
             if (j < end) att_stage_load(&stage_all[wib][q][lane], mt, mac, perm_t[j]);
             cp_async_commit();
         }
 #pragma unroll
         for (int q = 0; q < kAttStages; q++) {
-            const int64_t j = beg + lane + kWarp * (q + kAttStages);
+            const int64_t j = beg + sub + kAttLanes * (q + kAttStages);
             pnext[q] = j < end ? perm_t[j] : 0u;
         }
-        for (int64_t base = beg; base < end; base += kWarp * kAttStages) {
+        // the group's lanes run the same rounds (their own interval's length)
+        for (int64_t base = beg; base < end; base += kAttLanes * kAttStages) {
 #pragma unroll
           for (int q = 0; q < kAttStages; q++) {
-            const int64_t j = base + kWarp * q + lane;
+            const int64_t j = base + kAttLanes * q + sub;
             cp_async_wait<kAttStages - 1>();  // the oldest outstanding group: this stage
             AttStage& sg = stage_all[wib][q][lane];
             const MixT rt = sg.t;
             const float2 WR = sg.ac;          // (W, W R)
-            __syncwarp();
+            __syncwarp(gmask);
             // refill the stage with this lane's observation kAttStages rounds ahead
-            const int64_t jn = j + kWarp * kAttStages;
+            const int64_t jn = j + kAttLanes * kAttStages;
             if (jn < end) {
                 att_stage_load(&sg, mt, mac, pnext[q]);
-                const int64_t jf = jn + kWarp * kAttStages;
+                const int64_t jf = jn + kAttLanes * kAttStages;
                 pnext[q] = jf < end ? perm_t[jf] : 0u;
             }
             cp_async_commit();
@@ -879,21 +896,25 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
           }
         }
         cp_async_wait<0>();
-        // compensated cross-lane reduction through shared memory
+        // compensated reduction of the group's lane partials through shared memory
 #pragma unroll
         for (int k = 0; k < kAccVals; k++) red[lane * kAccPad + k] = acc[k];
         __syncwarp();
+        if (have) {
+            const float* gred = red + grp * kAttLanes * kAccPad;
+            for (int o = sub; o < kBlkVals; o += kAttLanes) {
+                const int src = src_tab[o];
+                float hi = 0.0f, lo = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 5; k++) {
-            if (src_idx[k] < 0) continue;
-            float hi = 0.0f, lo = 0.0f;
-            for (int q = 0; q < kWarp; q++) {
-                float s_, e_;
-                two_sum(hi, red[q * kAccPad + src_idx[k]], s_, e_);
-                hi = s_;
-                lo = __fadd_rn(lo, e_);
+                for (int q = 0; q < kAttLanes; q++) {
+                    float s_, e_;
+                    two_sum(hi, gred[q * kAccPad + src], s_, e_);
+                    hi = s_;
+                    lo = __fadd_rn(lo, e_);
+                }
+                const double v = (double)hi + (double)lo;
+                blk[(int64_t)iv * kBlkVals + o] = src >= 100 ? -v : v;
             }
-            blk[(int64_t)iv * kBlkVals + lane + 32 * k] = (double)sgn[k] * ((double)hi + (double)lo);
         }
         __syncwarp();
     }
@@ -1052,7 +1073,7 @@ void launch_mix_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const u
                           const int64_t* ivl_off, int n_iv, const MixObs& mo, const double* att, double* blk,
                           const Shapes& sh, cudaStream_t s) {
     const int bps = sh.att_bps > 0 ? sh.att_bps : 64;
-    k_mix_att_accum<<<grid_of(n_iv, kAttWarps, 152 * bps), 32 * kAttWarps, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t,
+    k_mix_att_accum<<<grid_of((n_iv + kAttGroups - 1) / kAttGroups, kAttWarps, 152 * bps), 32 * kAttWarps, 0, s>>>(G, (float)lambda2, rhs_norm, perm_t,
                                                                                  ivl_off, n_iv, mo.ac, mo.t, att, blk);
 }
 

@@ -226,6 +226,9 @@ __global__ void k_src_geo(int32_t n_src, const double* __restrict__ src, double*
         double* g = geo + 16 * (size_t)i;
         for (int k = 0; k < 3; k++) { g[k] = S.p[k]; g[3 + k] = S.q[k]; g[6 + k] = S.r[k]; }
         g[9] = S.par; g[10] = S.pma; g[11] = S.pmd; g[12] = S.cosd;
+        // slots 13-15: p and q rounded to FP32 (six floats)
+        float* gf = reinterpret_cast<float*>(g + 13);
+        for (int k = 0; k < 3; k++) { gf[k] = (float)S.p[k]; gf[3 + k] = (float)S.q[k]; }
     }
 }
 
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, int64_t n_obs, co
         const uint32_t m = meta[o];
         const double muv = meta_kind(m) ? mu[o] : 0.0;
         ObsOut ob;
-        observe<true>(G, S, t, m, muv, att, cal, ob);
+        observe<1>(G, S, t, m, muv, att, cal, ob);
         const double sg = (double)sigma[o];
         double* e = scr + (size_t)o * kScr;
         e[0] = ob.R;
@@ -560,7 +563,7 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
         source_geo(src + 5 * (size_t)obs_src[o], S);
         uint32_t m = meta[o];
         ObsOut ob;
-        observe<false>(G, S, t_ns[o], m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
+        observe<0>(G, S, t_ns[o], m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
         R[o] = ob.R;
     }
 }

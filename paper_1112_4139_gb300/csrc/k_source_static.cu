@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(128) k_source_static(DevGeo G, Settings st, Ob
                                         : (int64_t)n_days * 124 + (day * 2 + f) * AGIS_N_ROW + rows.row[c];
             const uint32_t m = (uint32_t)(c & 63) | ((uint32_t)f << 6) | ((uint32_t)k << 7) | ((uint32_t)kcal << 8);
             ObsOut oo;
-            observe<true>(G, S, t, m, k ? ob.mu[o] : 0.0, att, cal, oo);
+            observe<1>(G, S, t, m, k ? ob.mu[o] : 0.0, att, cal, oo);
             const double sg = (double)ob.sigma[o];
             double* e = scr + (size_t)j * kScr;
             e[0] = oo.R;
