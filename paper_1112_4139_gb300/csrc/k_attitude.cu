@@ -128,15 +128,16 @@ __global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, c
                                const int32_t* __restrict__ seg_n, const double* __restrict__ blk,
                                double* __restrict__ bandc, double* __restrict__ rhs) {
     const int64_t total = seg_row[n_seg] * 16;
+    const int64_t avg_rows = (seg_row[n_seg] + n_seg - 1) / n_seg > 0 ? (seg_row[n_seg] + n_seg - 1) / n_seg : 1;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = t >> 4;
         const int k = (int)(t & 15);
-        int lo = 0, hi = n_seg - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (seg_row[mid] <= row) lo = mid; else hi = mid - 1;
-        }
-        const int sg = lo;
+        // the segment of this row: the segments are of nearly equal length, so a guess from
+        // the average length and a step or two of correction replace a binary search
+        int sg = (int)(row / avg_rows);
+        if (sg > n_seg - 1) sg = n_seg - 1;
+        while (sg > 0 && seg_row[sg] > row) sg--;
+        while (sg < n_seg - 1 && seg_row[sg + 1] <= row) sg++;
         const int c = (int)(row - seg_row[sg]);
         const int l_lo = seg_l[2 * sg], l_hi = seg_l[2 * sg + 1];
         const int n_lo = seg_n[2 * sg];

@@ -263,9 +263,7 @@ __device__ __forceinline__ void class_sums(const MixS* rs, const float2* rr, int
 #pragma unroll
         for (int i = 0; i < 5; i++) Ah[i] = 0.0f;
         const int lo = c ? nal : 0, hi = c ? n : nal;
-        for (int j = lo + lane; j < hi; j += kWarp) {
-            const MixS r = rs[j];
-            const float Rh = rr[j].x;
+        auto add = [&](const MixS& r, float Rh) {
             float A[5];
             arow(r, A);
             const float hp = Rh - adot(A, in.dp);
@@ -279,7 +277,16 @@ __device__ __forceinline__ void class_sums(const MixS* rs, const float2* rr, int
                 Ah[a] = fmaf(wa, hp, Ah[a]);
             }
             hh = fmaf(w * hp, hp, hh);
+        };
+        // two records per lane in flight; the sums keep the order j, j + 32, ...
+        int j = lo + lane;
+        for (; j + kWarp < hi; j += 2 * kWarp) {
+            const MixS r0 = rs[j], r1 = rs[j + kWarp];
+            const float R0 = rr[j].x, R1 = rr[j + kWarp].x;
+            add(r0, R0);
+            add(r1, R1);
         }
+        if (j < hi) add(rs[j], rr[j].x);
 #pragma unroll
         for (int i = 0; i < 15; i++) AA[i] = warp_sum_f(AA[i]);
 #pragma unroll
@@ -694,15 +701,21 @@ __global__ void __launch_bounds__(32 * kW) k_mix_final(Settings st, const int64_
         float2* rr = mo.r + o0;
         float2* ac = mo.ac + o0;
         float chi = 0.0f;
-        for (int j = lane; j < n; j += kWarp) {
-            const MixS v = rs[j];
-            const float2 R = rr[j];
+        auto fin = [&](int jj, const MixS& v, float2 R) {
             float A[5];
             arow(v, A);
             const int cls = v.sig < 0.0f ? 1 : 0;
             const float wgt = round_weight(in, R.x, R.x - adot(A, in.dp), cls, st.weight_fn);
-            chi += apply_update(v, R, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]), rr + j, ac + j);
+            chi += apply_update(v, R, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]), rr + jj, ac + jj);
+        };
+        int j = lane;
+        for (; j + kWarp < n; j += 2 * kWarp) {
+            const MixS v0 = rs[j], v1 = rs[j + kWarp];
+            const float2 R0 = rr[j], R1 = rr[j + kWarp];
+            fin(j, v0, R0);
+            fin(j + kWarp, v1, R1);
         }
+        if (j < n) fin(j, rs[j], rr[j]);
         chi = warp_sum_f(chi);
         if (lane == 0) {
             out.chi2[i] = chi;
