@@ -167,116 +167,204 @@ __global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, c
     }
 }
 
-// Two segments per warp, one per 16-lane half: right-looking robust Cholesky (Algorithm C.1
-// on the envelope) with forward substitution (C.2) fused, then back substitution (C.3).
-// Lane b of a half holds column b of the sliding window W[a][b] = N[r+a][r+b] (a <= b); the
-// window moves one row per step by a shuffle within the half, and the column entering at
-// lane 15 comes from a shared-memory double buffer filled one block of 16 columns ahead.
-// The pivot's reciprocal is formed once per row and stored in place of U_rr for C.3.
+// Robust factorisation of each segment's band (Algorithm C.1 on the envelope, in the
+// square-root-free form N = V' D V with V unit upper triangular: U = sqrt(D) V, the same pivot
+// test on D and the same zeroed rows for a failing pivot) with the forward substitution (C.2)
+// fused, then the back substitution (C.3).  Without the square root the per-row chain that
+// bounds the recurrence (pivot, reciprocal, V_{r,r+1}, the next pivot's update) is about a
+// third as long.  One segment per group of 8 lanes, four per warp.  The 16x16 window W[a][b] = N'[r+a][r+b] (a <= b) of the
+// partly reduced matrix lives in shared memory, addressed by absolute row and column modulo
+// 16, so that moving the window by one row moves no data.  Per row the 120 window entries
+// below the pivot row are updated 15 per lane (every lane the same count, so one FP64
+// instruction of the warp does useful work in all its lanes), and the column that enters
+// the window comes from a ring filled by cp.async kColAhead rows ahead, each lane copying
+// and later consuming the same two entries.  Every entry receives the same FMAs in the
+// same order whatever the lane mapping, and the back substitution sums its 15 products in a
+// fixed tree.  Row r of urow holds 1/D_r and V_{r, r+1..r+15}; yv holds w_r / D_r.
+constexpr int kSegLanes = 8;
+constexpr int kSegsPerWarp = kWarp / kSegLanes;
 constexpr int kSolveSegWarps = 2;
+constexpr int kColAhead = 8;
+struct __align__(16) SegWin {
+    double W[16][16];            // W[row mod 16][col mod 16], upper part (row <= col) in use
+    double z[16];                // partly reduced right-hand side per row slot
+    double dg[16];               // original diagonal per row slot (the pivot test of C.1)
+    double U[16];                // the current row of V: U[b] = V_{r, r+b} (b >= 1)
+    double xs[16];               // back substitution: x of the rows r+1 .. r+15 by slot
+    double ring[kColAhead][18];  // incoming columns: 16 band values, rhs, pad
+    double pad[8];               // 3776 B: consecutive segments start 64 B apart modulo 128 B,
+                                 // so the two segments of a half warp use disjoint banks
+};
+static_assert(sizeof(SegWin) % 128 == 64, "segment windows must alternate between bank halves");
+
+__device__ __forceinline__ void cp_async16_att(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8_att(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_att() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_att() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// 1/d for d > 0 by two Newton-Raphson steps y <- y + y (1 - d y) from an FP32 seed: the
+// seed's relative error (below 2^-22: FP32 rounding of d and the approximate reciprocal) is
+// squared by each step, so the result is within the FP64 rounding of 1/d.  d outside
+// [2^-100, 2^100] (checked on the exponent bits) takes the plain division.
+__device__ __forceinline__ double rcp_pos(double d) {
+    const int ex = (__double2hiint(d) >> 20) & 0x7ff;
+    if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(__double2float_rn(d)));
+    double y = (double)y0;
+    y = fma(y, fma(-d, y, 1.0), y);
+    y = fma(y, fma(-d, y, 1.0), y);
+    return y;
+}
+
 __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
                                                   const double* __restrict__ bandc, const double* __restrict__ rhs,
                                                   double* __restrict__ urow, double* __restrict__ yv,
                                                   double* __restrict__ x, double tol, int* __restrict__ seg_rd) {
-    __shared__ double colbuf_all[kSolveSegWarps][2][2][16][17];
+    __shared__ SegWin win_all[kSolveSegWarps][kSegsPerWarp];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int half = lane >> 4;
-    const int b = lane & 15;
-    double (*colbuf)[16][17] = colbuf_all[wib][half];
-    const int sg = (blockIdx.x * kSolveSegWarps + wib) * 2 + half;
+    const int grp = lane / kSegLanes;
+    const int sub = lane % kSegLanes;
+    const unsigned gmask = ((1u << kSegLanes) - 1u) << (grp * kSegLanes);
+    SegWin& sm = win_all[wib][grp];
+    const int sg = (blockIdx.x * kSolveSegWarps + wib) * kSegsPerWarp + grp;
     const bool seg_ok = sg < n_seg;
     const int64_t base = seg_ok ? seg_row[sg] : 0;
     const int64_t n = seg_ok ? seg_row[sg + 1] - base : 0;
-    const int64_t n_other = __shfl_xor_sync(0xffffffffu, n, 16);
-    const int64_t n_max = n > n_other ? n : n_other;
+    int64_t n_max = n;
+#pragma unroll
+    for (int o = kSegLanes; o < kWarp; o <<= 1) {
+        const int64_t v = __shfl_xor_sync(0xffffffffu, n_max, o);
+        n_max = v > n_max ? v : n_max;
+    }
     if (n_max == 0) return;
-    const unsigned FULL = 0xffffffffu;
-    double pre[17];
-    auto load_block = [&](int64_t kb) {
-        const int64_t c = 16 * kb + b;
-        const bool ok = c < n;
+    // this lane's 15 window entries per row, (a, b) with 1 <= a <= b <= 15 in row-major
+    // order: pair p = 8 t + sub (the a = 1 row, which the next pivot needs, comes first)
+    int pa[15], pb[15];
 #pragma unroll
-        for (int a = 0; a < 16; a++) pre[a] = ok ? bandc[(base + c) * 16 + a] : 0.0;
-        pre[16] = ok ? rhs[base + c] : 0.0;
-    };
-    auto store_block = [&](int64_t kb) {
+    for (int t = 0; t < 15; t++) {
+        int p = kSegLanes * t + sub, a = 1;
+        while (p >= 16 - a) { p -= 16 - a; a++; }
+        pa[t] = a;
+        pb[t] = a + p;
+    }
+    // initial window: rows and columns 0..15 (lane sub loads columns 2 sub and 2 sub + 1)
 #pragma unroll
-        for (int a = 0; a < 17; a++) colbuf[kb & 1][b][a] = pre[a];
-        __syncwarp();
-    };
-    double w[16];
+    for (int h = 0; h < 2; h++) {
+        const int b = 2 * sub + h;
+        for (int a = 0; a < 16; a++)
+            sm.W[a][b] = (a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
+        sm.dg[b] = b < n ? bandc[(base + b) * 16] : 0.0;
+        sm.z[b] = b < n ? rhs[base + b] : 0.0;
+    }
+    // the columns 16 .. 16 + kColAhead - 1 into the ring (lane sub: band entries 2 sub, 2 sub + 1;
+    // lane 0 also the right-hand side)
 #pragma unroll
-    for (int a = 0; a < 16; a++) w[a] = (a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
-    double dg = b < n ? bandc[(base + b) * 16] : 0.0;
-    double z = b < n ? rhs[base + b] : 0.0;
-    load_block(1);
-    store_block(1);
-    load_block(2);
+    for (int q = 0; q < kColAhead; q++) {
+        const int64_t c = 16 + q;
+        if (c < n) {
+            cp_async16_att(&sm.ring[q][2 * sub], bandc + (base + c) * 16 + 2 * sub);
+            if (sub == 0) cp_async8_att(&sm.ring[q][16], rhs + base + c);
+        }
+        cp_async_commit_att();
+    }
+    __syncwarp();
     int rd = 0;
     for (int64_t r = 0; r < n_max; r++) {
-        if (r >= 16 && (r & 15) == 0) {
-            const int64_t m = r >> 4;
-            store_block(m + 1);
-            load_block(m + 2);
-        }
         const bool live = r < n;
-        const double piv = __shfl_sync(FULL, w[0], 0, 16);
-        const double dg0 = __shfl_sync(FULL, dg, 0, 16);
-        const double urr = piv > tol * dg0 ? sqrt(piv) : 0.0;
-        const double inv = urr > 0.0 ? 1.0 / urr : 0.0;
-        if (live) rd += urr == 0.0;
-        double myU = (b == 0) ? urr : w[0] * inv;
-        if (r + b >= n && b > 0) myU = 0.0;
-        const double zr = __shfl_sync(FULL, z, 0, 16);
-        const double yr = zr * inv;
-        if (live) {
-            urow[(base + r) * 16 + b] = (b == 0) ? inv : myU;
-            if (b == 0) yv[base + r] = yr;
-        }
-        if (b >= 1) z -= myU * yr;
+        const int s0 = (int)(r & 15);
+        const double piv = sm.W[s0][s0];
+        const double dg0 = sm.dg[s0];
+        // the pivot test of Algorithm C.1; a failing pivot zeroes the row (rank defect)
+        const bool pos = piv > tol * dg0;
+        const double invd = (pos && piv > 0.0) ? rcp_pos(piv) : 0.0;
+        if (live) rd += !pos;
+        const double wr = sm.z[s0];
+        const double yr = wr * invd;
+        // V_{r, r+b} = W[0][b] / D_r and the forward substitution z_b -= V_b w_r, b = sub + 1, sub + 9
 #pragma unroll
-        for (int a = 1; a < 16; a++) {
-            const double ua = __shfl_sync(FULL, myU, a, 16);
-            if (a <= b) w[a] -= ua * myU;
-        }
-#pragma unroll
-        for (int a = 0; a < 15; a++) w[a] = __shfl_down_sync(FULL, w[a + 1], 1, 16);
-        w[15] = 0.0;
-        z = __shfl_down_sync(FULL, z, 1, 16);
-        dg = __shfl_down_sync(FULL, dg, 1, 16);
-        if (b == 15) {
-            const int64_t c = r + 16;
-            if (c < n) {
-                const double* col = colbuf[(c >> 4) & 1][c & 15];
-#pragma unroll
-                for (int a = 0; a < 16; a++) w[a] = col[15 - a];
-                dg = col[0];
-                z = col[16];
-            } else {
-#pragma unroll
-                for (int a = 0; a < 16; a++) w[a] = 0.0;
-                dg = 0.0;
-                z = 0.0;
+        for (int h = 0; h < 2; h++) {
+            const int b = sub + 1 + kSegLanes * h;
+            if (b <= 15) {
+                const int sb = (int)((r + b) & 15);
+                double v = sm.W[s0][sb] * invd;
+                if (r + b >= n) v = 0.0;
+                sm.U[b] = v;
+                sm.z[sb] -= v * wr;
             }
         }
-    }
-    // back substitution: lane b of the half holds x_{r+b} (b >= 1); slot 0 of a U row holds 1/U_rr
-    double xw = 0.0;
-    for (int64_t k = 0; k < n_max; k++) {
-        const int64_t r = n - 1 - k;
-        const bool live = r >= 0;
-        const double ur = live ? urow[(base + r) * 16 + b] : 0.0;
-        double part = (b >= 1) ? ur * xw : 0.0;
+        __syncwarp(gmask);
+        if (live) {
+            const double v0 = sub == 0 ? invd : sm.U[2 * sub];
+            *reinterpret_cast<double2*>(urow + (base + r) * 16 + 2 * sub) = make_double2(v0, sm.U[2 * sub + 1]);
+            if (sub == 0) yv[base + r] = yr;
+        }
+        // the window below the pivot row: W[a][b] -= V_a W[0][b] (= W[0][a] W[0][b] / D_r);
+        // row r's slot is not written in this step
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o, 16);
-        const double inv = __shfl_sync(FULL, ur, 0, 16);
-        const double xr = live ? (yv[base + r] - part) * inv : 0.0;
-        if (live && b == 0) x[base + r] = xr;
-        xw = __shfl_up_sync(FULL, xw, 1, 16);
-        if (b == 1) xw = xr;
+        for (int t = 0; t < 15; t++) {
+            const int a = pa[t], b = pb[t];
+            const int sb = (int)((r + b) & 15);
+            double& w = sm.W[(r + a) & 15][sb];
+            w -= sm.U[a] * sm.W[s0][sb];
+        }
+        // the column r + 16 enters in the slot of column r (row r's entries are no longer read)
+        cp_async_wait_att<kColAhead - 1>();
+        const int64_t c = r + 16;
+        const int q = (int)(r % kColAhead);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int k = 2 * sub + h;   // band entry N[c - k][c]: window row a = 15 - k
+            const int a = 15 - k;
+            sm.W[(r + 1 + a) & 15][s0] = c < n ? sm.ring[q][k] : 0.0;
+        }
+        if (sub == 0) {
+            sm.dg[s0] = c < n ? sm.ring[q][0] : 0.0;
+            sm.z[s0] = c < n ? sm.ring[q][16] : 0.0;
+        }
+        __syncwarp(gmask);
+        // refill the ring slot (read above by this lane only) with the column kColAhead on
+        const int64_t cn = c + kColAhead;
+        if (cn < n) {
+            cp_async16_att(&sm.ring[q][2 * sub], bandc + (base + cn) * 16 + 2 * sub);
+            if (sub == 0) cp_async8_att(&sm.ring[q][16], rhs + base + cn);
+        }
+        cp_async_commit_att();
     }
-    if (b == 0 && seg_ok) seg_rd[sg] = rd;
+    cp_async_wait_att<0>();
+    // back substitution: x_r = y_r - sum_k V_{r,r+k} x_{r+k}, k = 1..15, y_r = w_r / D_r; lane
+    // sub forms the products k = sub and sub + 8 and the group adds them in a fixed tree
+    for (int k = 0; k < 16; k++)
+        if (sub == 0) sm.xs[k] = 0.0;
+    __syncwarp();
+    for (int64_t kk = 0; kk < n_max; kk++) {
+        const int64_t r = n - 1 - kk;
+        const bool live = r >= 0;
+        const double* ur = urow + (base + (live ? r : 0)) * 16;
+        const double p_lo = (live && sub >= 1) ? ur[sub] * sm.xs[(r + sub) & 15] : 0.0;
+        const double p_hi = live ? ur[sub + 8] * sm.xs[(r + sub + 8) & 15] : 0.0;
+        double part = p_lo + p_hi;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, kSegLanes);
+        const double xr = live ? yv[base + r] - part : 0.0;
+        __syncwarp(gmask);
+        if (live && sub == 0) {
+            x[base + r] = xr;
+            sm.xs[r & 15] = xr;
+        }
+        __syncwarp(gmask);
+    }
+    if (sub == 0 && seg_ok) seg_rd[sg] = rd;
 }
 
 // a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per
@@ -320,7 +408,7 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
     k_att_assemble<<<blocks, 256, 0, s>>>(n_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
-    const int seg_warps = (n_seg + 1) / 2;
+    const int seg_warps = (n_seg + kSegsPerWarp - 1) / kSegsPerWarp;
     k_att_solve<<<(seg_warps + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
         n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
     k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att, d_att);

@@ -558,9 +558,8 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
         const float2* rr = mo.r + o0;
         const bool in_smem = n <= kKeyCap;
         float lo[2] = {3.0e38f, 3.0e38f}, hi[2] = {0.0f, 0.0f};
-        for (int j = lane; j < n; j += kWarp) {
-            const float sg = rs[j].sig;
-            if (in_smem) skeys[j] = fkey(rr[j].x / fabsf(sg));
+        auto scan = [&](int jj, float sg, float Rh) {
+            if (in_smem) skeys[jj] = fkey(Rh / fabsf(sg));
             if (sg < 0.0f) {
                 lo[1] = fminf(lo[1], -sg);
                 hi[1] = fmaxf(hi[1], -sg);
@@ -568,7 +567,15 @@ __global__ void __launch_bounds__(32 * kScaleWarps) k_mix_scale_sums(Settings st
                 lo[0] = fminf(lo[0], sg);
                 hi[0] = fmaxf(hi[0], sg);
             }
+        };
+        int j = lane;
+        for (; j + kWarp < n; j += 2 * kWarp) {   // two records in flight per lane
+            const float sg0 = rs[j].sig, sg1 = rs[j + kWarp].sig;
+            const float R0 = rr[j].x, R1 = rr[j + kWarp].x;
+            scan(j, sg0, R0);
+            scan(j + kWarp, sg1, R1);
         }
+        if (j < n) scan(j, rs[j].sig, rr[j].x);
 #pragma unroll
         for (int c = 0; c < 2; c++)
 #pragma unroll
@@ -840,9 +847,11 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
 #pragma unroll
         for (int k = 0; k < 16; k++)
             a[k] = __shfl_sync(0xffffffffu, k < kAttLanes ? af0 : af1, grp * kAttLanes + (k & (kAttLanes - 1)));
-        float acc[kAccVals];
+        // accumulators as pairs: acc2[k] = (acc[2k], acc[2k+1]); two-wide FP32 FMAs (each lane
+        // of the pair rounds like fmaf) halve the FMA instructions of the issue-bound loop
+        float2 acc2[kAccVals / 2];
 #pragma unroll
-        for (int k = 0; k < kAccVals; k++) acc[k] = 0.0f;
+        for (int k = 0; k < kAccVals / 2; k++) acc2[k] = make_float2(0.0f, 0.0f);
         const int64_t beg = have ? ivl_off[iv] : 0, end = have ? ivl_off[iv + 1] : 0;
         // prologue: this lane's first kAttStages observations into the stages, and the indices
         // of the next kAttStages into registers
@@ -899,19 +908,28 @@ __global__ void __launch_bounds__(32 * kAttWarps) k_mix_att_accum(DevGeo G, floa
                 if (rhs_norm) r[c] -= W * (2.0f * lambda2 * D * s[c]);
             }
 #pragma unroll
-            for (int p = 0; p < 10; p++)
+            for (int p = 0; p < 10; p++) {
+                const float2 bb = make_float2(BB[p], BB[p]);
 #pragma unroll
-                for (int m = 0; m < 10; m++) acc[p * 10 + m] = fmaf(BB[p], M[m], acc[p * 10 + m]);
+                for (int m = 0; m < 10; m += 2)
+                    acc2[(p * 10 + m) / 2] = __ffma2_rn(bb, make_float2(M[m], M[m + 1]), acc2[(p * 10 + m) / 2]);
+            }
 #pragma unroll
-            for (int b = 0; b < 4; b++)
+            for (int b = 0; b < 4; b++) {
+                const float2 bv = make_float2(B[b], B[b]);
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[100 + 4 * b + c] = fmaf(B[b], r[c], acc[100 + 4 * b + c]);
+                for (int c = 0; c < 4; c += 2)
+                    acc2[(100 + 4 * b + c) / 2] = __ffma2_rn(bv, make_float2(r[c], r[c + 1]), acc2[(100 + 4 * b + c) / 2]);
+            }
           }
         }
         cp_async_wait<0>();
         // compensated reduction of the group's lane partials through shared memory
 #pragma unroll
-        for (int k = 0; k < kAccVals; k++) red[lane * kAccPad + k] = acc[k];
+        for (int k = 0; k < kAccVals / 2; k++) {
+            red[lane * kAccPad + 2 * k] = acc2[k].x;
+            red[lane * kAccPad + 2 * k + 1] = acc2[k].y;
+        }
         __syncwarp();
         if (have) {
             const float* gred = red + grp * kAttLanes * kAccPad;
