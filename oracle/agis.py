@@ -5,6 +5,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import blocks as B
+from . import model as M
 
 
 @dataclass
@@ -33,18 +34,29 @@ class IterStats:
 def iterate_once(P, state, st, ref=None, after_s=None):
     """One AGIS iteration in the order of Sect. 4.6: s^(k+1) from a^(k), c^(k); then a^(k+1)
     and c^(k+1) both from s^(k+1) with the old a^(k), c^(k); then the frame rotator.
+    st.block_order selects the variants of Sect. 4.6 (see blocks.Settings).
     after_s(src1, sres, ev) -> (src1, R), if given, changes the sources after the S block and
     returns the residuals the A and C blocks read (the accelerated iteration, Sect. 4.7)."""
     src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st)
     R = sres.R
     if after_s is not None:
         src1, R = after_s(src1, sres, ev)
+    if st.block_order == "[SAC]":
+        R = ev["R"]                     # Jacobi: the residuals at the previous iterate
     att1, rda = state.att.copy(), 0
     cal1, rdc = state.cal.copy(), 0
     if "A" in st.block_mask:
         att1, rda = B.attitude_update(P, state.att, ev, R, sres.W, st)
+    Rc = R
+    if st.block_order == "SAC":
+        # Gauss-Seidel: C sees the attitude update through the linearised residuals,
+        # R + (dR/da) (a^(k+1) - a^(k)) (the N_ca block of Eq. precond)
+        Ga = M.attitude_design(ev).reshape(P.n_obs, 16)
+        da = (att1 - state.att).reshape(-1)
+        cols = 4 * (ev["l"][:, None] - 3) + np.arange(16)
+        Rc = R + np.sum(Ga * da[cols], axis=1)
     if "C" in st.block_mask:
-        cal1, rdc = B.calibration_update(P, state.cal, ev, R, sres.W)
+        cal1, rdc = B.calibration_update(P, state.cal, ev, Rc, sres.W)
     frame = np.zeros(6)
     if st.frame_each_iter and ref is not None:
         eps, om = B.frame_fit(P, src1, ref)

@@ -52,6 +52,11 @@ class Settings:
     seg_overlap: int = 12        # L
     block_mask: str = "SAC"      # blocks run by an iteration
     frame_each_iter: bool = True
+    # order of the blocks within an iteration (Sect. 4.6): "S[AC]" A and C from the residuals
+    # after the source update (Eq. precondS(CAG)); "SAC" C also after the attitude update
+    # (Gauss-Seidel, Eq. precond); "[SAC]" A and C from the residuals before the source
+    # update (Jacobi, Eq. precond(SCAG))
+    block_order: str = "S[AC]"
 
 
 def _wfun(st):

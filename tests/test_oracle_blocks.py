@@ -107,11 +107,15 @@ def _reduced_solve(Nm, b):
     return x
 
 
-def test_one_iteration_equals_preconditioner_solve():
+@pytest.mark.parametrize("order", ["S[AC]", "SAC", "[SAC]"])
+def test_one_iteration_equals_preconditioner_solve(order):
+    # the three block orders of Sect. 4.6: S[AC] (Eq. precondS(CAG), N_as and N_cs below the
+    # diagonal), SAC (Gauss-Seidel, Eq. precond: also N_ca) and [SAC] (Jacobi, Eq.
+    # precond(SCAG): block diagonal)
     ds = synth.simulate(synth.config("small1yr", n_src=6000, span_days=180, min_transits=6, seed=11))
     P = M.problem_from_dataset(ds)
     K = P.n_coef - 3
-    st = B.Settings(robust=False, seg_len=K + 10, lam=1e-3, frame_each_iter=False)
+    st = B.Settings(robust=False, seg_len=K + 10, lam=1e-3, frame_each_iter=False, block_order=order)
     state = G.State(ds.src0.copy(), ds.att0.copy(), ds.cal0.copy())
     new, stats, sres = G.iterate_once(P, state, st)
     ev = M.evaluate(P, state.src, state.att, state.cal)
@@ -123,7 +127,9 @@ def test_one_iteration_equals_preconditioner_solve():
     ds_ = _reduced_solve(Nss, bs)
     assert np.allclose(ds_.reshape(-1, 5), sres.d, rtol=1e-7, atol=1e-6 * np.abs(sres.d).max())
     Naa = (Ja.T @ Wm @ Ja + st.lam ** 2 * (Jd.T @ Wm @ Jd)).tocsc()
-    ba = -(Ja.T @ (Wm @ R0)) - (Ja.T @ Wm @ Js) @ ds_
+    ba = -(Ja.T @ (Wm @ R0))
+    if order != "[SAC]":
+        ba = ba - (Ja.T @ Wm @ Js) @ ds_
     da = _reduced_solve(Naa, ba)
     # compare where the data determine the update: its effect on the residuals, J_a d_a
     # (directions with J_a v ~ 0, e.g. the spline scale regularised only by lambda^2, are
@@ -132,7 +138,11 @@ def test_one_iteration_equals_preconditioner_solve():
     yr = Ja @ da
     assert np.linalg.norm(ya - yr) < 1e-6 * np.linalg.norm(yr)
     Ncc = (Jc.T @ Wm @ Jc).diagonal()
-    bc = -(Jc.T @ (Wm @ R0)) - (Jc.T @ Wm @ Js) @ ds_
+    bc = -(Jc.T @ (Wm @ R0))
+    if order != "[SAC]":
+        bc = bc - (Jc.T @ Wm @ Js) @ ds_
+    if order == "SAC":
+        bc = bc - (Jc.T @ Wm @ Ja) @ da
     dc = np.where(Ncc > 0, bc / np.where(Ncc > 0, Ncc, 1), 0.0)
     for g in B.calibration_constraint_groups(P):
         dc[g] -= dc[g].mean()
