@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--asi", action="store_true",
                     help="with --convergence: also the accelerated simple iteration (Sect. 4.7) in both forms")
     ap.add_argument("--asi-stride", type=int, default=16, help="ASI: every n-th source enters the lambda estimate")
+    ap.add_argument("--orders", action="store_true",
+                    help="with --convergence: also the Gauss-Seidel and Jacobi block orders (Sect. 4.6), mixed form")
     ap.add_argument("--asi-lambda-max", type=float, default=0.9, help="ASI: clamp of the lambda estimate")
     return ap.parse_args()
 
@@ -307,9 +309,9 @@ def run_convergence(args, agis, ds, stream, rank):
         e[:, 0] = (np.mod(e[:, 0] + np.pi, 2 * np.pi) - np.pi) * cosd
         return e / UAS
 
-    def open_form(prec):
+    def open_form(prec, order=0):
         cfg = agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, precision=prec,
-                                  refresh_every=args.refresh_every)
+                                  refresh_every=args.refresh_every, block_order=order)
         return agis.Agis(ds.geometry, cfg, agis.obs_from_dataset(ds), np.ascontiguousarray(ds.src0),
                          np.ascontiguousarray(ds.att0), np.ascontiguousarray(ds.cal0), src_ref=ref,
                          stream=stream.cuda_stream)
@@ -351,8 +353,8 @@ def run_convergence(args, agis, ds, stream, rank):
 
     it64, s64 = first_below(rms64, t64)
     # the other runs against the same reference
-    def run_mixed(params=None, extra=3, asi=False, prec=1):
-        g = open_form(prec)
+    def run_mixed(params=None, extra=3, asi=False, prec=1, order=0):
+        g = open_form(prec, order)
         if params is not None:
             g.set_proposal(params, args.proposal_every)
         if asi:
@@ -413,6 +415,15 @@ def run_convergence(args, agis, ds, stream, rank):
                                "stride": args.asi_stride, "lambda_max": args.asi_lambda_max,
                                "factors": [round(v, 3) for v in fac], "rms_uas": [round(v, 4) for v in rmsa],
                                "per_param_rms_uas_at_1uas": per_a}
+    order_lines = {}
+    if args.orders:
+        # the block orders of Sect. 4.6 in the mixed form: Gauss-Seidel SAC and Jacobi [SAC]
+        for name, order in (("mixed_gauss_seidel", 1), ("mixed_jacobi", 2)):
+            rmso, to, _, per_o = run_mixed(order=order)
+            ito, so = first_below(rmso, to)
+            order_lines[name] = {"iterations": ito, "seconds": so, "ms_per_iter": float(np.median(to)),
+                                 "block_order": order, "rms_uas": [round(v, 4) for v in rmso],
+                                 "per_param_rms_uas_at_1uas": per_o}
     line = {"metric": "wall time to 1 uas RMS vs FP64 reference", "unit": "s", "higher_is_better": False,
             "workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n_obs": ds.n_obs, "n_src": ds.n_src,
             "reference": {"form": "fp64", "iterations": len(rms64), "last_max_update_uas": ref_last_update,
@@ -424,6 +435,7 @@ def run_convergence(args, agis, ds, stream, rank):
                       "per_param_rms_uas_at_1uas": per_param},
             "speedup": (s64 / sm) if (s64 and sm) else None}
     line.update(asi_lines)
+    line.update(order_lines)
     if "fp64_asi" in asi_lines and s64 and asi_lines["fp64_asi"]["seconds"]:
         line["speedup_fp64_asi_vs_fp64"] = s64 / asi_lines["fp64_asi"]["seconds"]
     if "mixed_asi" in asi_lines and s64 and asi_lines["mixed_asi"]["seconds"]:

@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 5
+#define AGIS_ABI_VERSION 6
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -76,8 +76,17 @@ typedef struct agis_config {
     int32_t max_obs_per_source;  /* largest n_i accepted (bounds the S-pass scratch), 0: derived */
     int32_t precision;           /* 0: FP64 throughout; 1: mixed (see below)                 */
     int32_t refresh_every;       /* mixed: full FP64 residual refresh every n source updates */
-    int32_t reserved[5];
+    int32_t block_order;         /* 0: S[AC], 1: Gauss-Seidel SAC, 2: Jacobi [SAC] (below) */
+    int32_t reserved[4];
 } agis_config;
+
+/* Block order within an iteration (Sect. 4.6).  0, S[AC] (Eq. precondS(CAG)): A and C both
+ * from the residuals after the source update, R = h - A d.  1, SAC (block Gauss-Seidel, Eq.
+ * precond): C from those residuals with the attitude update added to first order,
+ * R + (dR/da) (a^(k+1) - a^(k)) (the N_ca block).  2, [SAC] (block Jacobi, Eq.
+ * precond(SCAG)): A and C from the residuals before the source update, R = h.  All three
+ * use the weights of the source update.  The learned proposal and ASI extrapolate the
+ * source update for A and C to read and need orders 0 or 1. */
 
 /* Mixed precision (precision = 1).  The residuals stay FP64; partials and normal-equation
  * accumulation run in FP32, and the outer block iteration acts as iterative refinement.

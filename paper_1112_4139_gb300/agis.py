@@ -19,7 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 5  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 6  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -52,7 +52,8 @@ class Config(C.Structure):
         ("lambda_att", C.c_double), ("rhs_norm_term", C.c_int32), ("seg_len", C.c_int32),
         ("seg_overlap", C.c_int32), ("frame_each_iter", C.c_int32), ("block_mask", C.c_int32),
         ("use_graph", C.c_int32), ("pivot_tol", C.c_double), ("max_obs_per_source", C.c_int32),
-        ("precision", C.c_int32), ("refresh_every", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("precision", C.c_int32), ("refresh_every", C.c_int32), ("block_order", C.c_int32),
+        ("reserved", C.c_int32 * 4),
     ]
 
 

@@ -27,7 +27,9 @@ void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint3
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
-                      cudaStream_t s);
+                      double* dx, cudaStream_t s);
+void launch_rec_att_correct(const DevGeo& G, int64_t n_obs, ObsRec* rec, const double* dx, cudaStream_t s);
+void launch_mix_ac_correct(const DevGeo& G, int64_t n_obs, const MixObs& mo, const float* d_att, cudaStream_t s);
 void launch_mix_pass(const DevGeo& G, bool refresh, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, const MixObs& mo, double* geo, float* d_att,
@@ -235,6 +237,7 @@ struct agis_ctx {
     bool mixed = false;
     MixObs mo{};
     float* d_att = nullptr;
+    double* datt64 = nullptr;     // FP64 form, block Gauss-Seidel: this iteration's attitude update
     float2* d_cal = nullptr;
     MixSrcWork mw{};
     bool mix_stale = true;   // the records do not describe the current state: evaluate in full
@@ -452,6 +455,9 @@ void enqueue_s_solve(agis_ctx* c) {
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
+    // block Gauss-Seidel, FP64 form: the attitude update C will see is this iteration's (none
+    // until an A block runs)
+    if (c->datt64) cudaMemsetAsync(c->datt64, 0, sizeof(double) * 4 * (size_t)c->n_coef, c->stream);
 }
 // learned proposal after the S block: features, network, sources += correction, and the
 // residuals that A and C read -= A correction
@@ -484,10 +490,17 @@ void enqueue_a(agis_ctx* c) {
                          c->rec, c->att, c->blk, c->sh, c->stream);
     launch_att_solve(c->n_seg, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
                      c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->mixed ? c->d_att : nullptr,
-                     c->stream);
+                     c->datt64, c->stream);
     launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
 }
 void enqueue_c(agis_ctx* c) {
+    // block Gauss-Seidel (Eq. precond): the residuals C reads take the attitude update
+    if (c->cfg.block_order == 1) {
+        if (c->mixed)
+            launch_mix_ac_correct(c->G, c->n_obs, c->mo, c->d_att, c->stream);
+        else
+            launch_rec_att_correct(c->G, c->n_obs, c->rec, c->datt64, c->stream);
+    }
     if (c->mixed)
         launch_mix_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->mo, c->dtil, c->cal_rd, c->cal, c->d_cal,
                        c->sh, c->stream);
@@ -648,6 +661,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     if (cfg->precision != 0 && cfg->precision != 1) return bail(fail(c, AGIS_E_INVALID, "precision must be 0 or 1"));
     if (cfg->precision == 1 && cfg->refresh_every < 1)
         return bail(fail(c, AGIS_E_INVALID, "refresh_every must be at least 1"));
+    if (cfg->block_order < 0 || cfg->block_order > 2)
+        return bail(fail(c, AGIS_E_INVALID, "block_order must be 0 (S[AC]), 1 (SAC) or 2 ([SAC])"));
     for (int i = 0; i < AGIS_N_CCD; i++)
         if (geo->ccd_row[i] < 0 || geo->ccd_row[i] >= AGIS_N_ROW) return bail(fail(c, AGIS_E_INVALID, "bad ccd_row"));
     c->geo = *geo;
@@ -676,6 +691,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     st.lambda2 = cfg->lambda_att * cfg->lambda_att;
     st.rhs_norm_term = cfg->rhs_norm_term;
     st.pivot_tol = cfg->pivot_tol;
+    st.handover_h = cfg->block_order == 2 ? 1 : 0;
     for (int i = 0; i < agis_ctx::kEvents; i++) cudaEventCreate(&c->ev[i]);
     if (cudaMallocHost(&c->hstat, 32 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->hisum, 4 * sizeof(long long)) != cudaSuccess)
@@ -843,6 +859,10 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
             return bail(rc);
     } else {
         if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
+        if (cfg->block_order == 1) {
+            if ((rc = dalloc(c, &c->datt64, 4 * (size_t)n_coef))) return bail(rc);
+            cudaMemsetAsync(c->datt64, 0, sizeof(double) * 4 * (size_t)n_coef, s);
+        }
     }
     if ((rc = dalloc(c, &c->sgeo, 16 * (size_t)n_src)) ||
         (rc = dalloc(c, &c->work, 4)) || (rc = dalloc(c, &c->so.d, 5 * (size_t)n_src)) ||
@@ -1223,6 +1243,8 @@ int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
         return AGIS_OK;
     }
     if (every < 5) return fail(c, AGIS_E_INVALID, "proposal period below 5 iterations");
+    if (c->cfg.block_order == 2)
+        return fail(c, AGIS_E_INVALID, "the learned proposal needs block order S[AC] or SAC");
     if (!c->prop_packed) {
         void* packed = nullptr;
         AGIS_TRY(dalloc(c, reinterpret_cast<uint8_t**>(&packed), AGIS_MLP_PACKED_BYTES));
@@ -1258,6 +1280,7 @@ int agis_set_asi(agis_ctx* c, int32_t stride, double lambda_max) {
         return AGIS_OK;
     }
     if (!(lambda_max >= 0.0 && lambda_max < 1.0)) return fail(c, AGIS_E_INVALID, "lambda_max outside [0, 1)");
+    if (c->cfg.block_order == 2) return fail(c, AGIS_E_INVALID, "ASI needs block order S[AC] or SAC");
     if (!c->asi_keys) {
         const size_t n_s = std::max<size_t>(1, ((size_t)c->n_src + stride - 1) / stride);
         AGIS_TRY(dalloc(c, &c->asi_keys, std::max<size_t>(n_s, (size_t)c->n_src)));

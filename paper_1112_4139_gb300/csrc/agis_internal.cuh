@@ -167,6 +167,7 @@ struct Settings {
     double lambda2;
     int rhs_norm_term;
     double pivot_tol;
+    int handover_h;   // block Jacobi: A and C read h (the residual before the source update)
 };
 
 // Launch shapes chosen by the autotuner.  Every kernel they shape gives each observation,

@@ -368,10 +368,11 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
 }
 
 // a_n += x for the coefficients each segment owns (n in [u_lo, u_hi]); one thread per
-// coefficient.  The mixed form also accumulates the update in d_att (FP32).
+// coefficient.  The mixed form also accumulates the update in d_att (FP32); dx, if given,
+// receives the update itself (FP64).
 __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ seg_u, const int32_t* __restrict__ seg_n,
                             const int64_t* __restrict__ seg_row, const double* __restrict__ x,
-                            double* __restrict__ att, float* __restrict__ d_att) {
+                            double* __restrict__ att, float* __restrict__ d_att, double* __restrict__ dx) {
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < n_coef; n += gridDim.x * blockDim.x) {
         int lo = 0, hi = n_seg - 1;
         while (lo < hi) {
@@ -384,6 +385,7 @@ __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ s
         for (int c = 0; c < 4; c++) {
             att[4 * (int64_t)n + c] += x[r0 + c];
             if (d_att) d_att[4 * (int64_t)n + c] += (float)x[r0 + c];
+            if (dx) dx[4 * (int64_t)n + c] = x[r0 + c];
         }
     }
 }
@@ -402,7 +404,7 @@ void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint3
 void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
-                      cudaStream_t s) {
+                      double* dx, cudaStream_t s) {
     int64_t total = n_rows * 16;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
@@ -411,7 +413,31 @@ void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_
     const int seg_warps = (n_seg + kSegsPerWarp - 1) / kSegsPerWarp;
     k_att_solve<<<(seg_warps + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
         n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
-    k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att, d_att);
+    k_att_apply<<<(n_coef + 255) / 256, 256, 0, s>>>(n_coef, n_seg, seg_u, seg_n, seg_row, x, att, d_att, dx);
+}
+
+// Block Gauss-Seidel (Sect. 4.6, Eq. precond): before the C block the hand-over residuals
+// take the attitude update to first order, R += sum_j B_j g . dx[l-3+j] (dR/da_n = g B_n,
+// Eq. dfadq); one thread per observation, FP64.
+__global__ void k_rec_att_correct(DevGeo G, int64_t n_obs, ObsRec* __restrict__ rec, const double* __restrict__ dx) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
+        ObsRec& r = rec[o];
+        const int l = left_index(G, r.t_ns);
+        double B[4];
+        bspline4(G, r.t_ns, l, B);
+        const double* d = dx + 4 * (int64_t)(l - 3);
+        double corr = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            corr += B[j] * (r.g[0] * d[4 * j] + r.g[1] * d[4 * j + 1] + r.g[2] * d[4 * j + 2] + r.g[3] * d[4 * j + 3]);
+        r.R += corr;
+    }
+}
+void launch_rec_att_correct(const DevGeo& G, int64_t n_obs, ObsRec* rec, const double* dx, cudaStream_t s) {
+    int64_t b = (n_obs + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    k_rec_att_correct<<<(int)b, 256, 0, s>>>(G, n_obs, rec, dx);
 }
 
 }  // namespace agis

@@ -363,14 +363,15 @@ __device__ __forceinline__ void gen_q(const MixS* rs, const float2* rr, const fl
 
 // R <- R - A d (float-pair arithmetic), the A/C inputs (W, W Rh), and the chi^2 term
 __device__ __forceinline__ float apply_update(const MixS& v, float2 R, const float* dh, const float* dl, float W,
-                                              float2* rr, float2* ac) {
+                                              float2* rr, float2* ac, int handover_h) {
     float A[5];
     arow(v, A);
     float sh, sl;
+    const float h = R.x;
     row_dot_pair(A, dh, dl, sh, sl);
     pair_add(R.x, R.y, -sh, -sl);
     *rr = R;
-    *ac = make_float2(W, W * R.x);
+    *ac = make_float2(W, W * (handover_h ? h : R.x));
     return W * R.x * R.x;
 }
 
@@ -446,7 +447,7 @@ __device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n,
     float chi = 0.0f;
     for (int j = lane; j < n; j += kWarp) {
         const MixS v = rs[j];
-        chi += apply_update(v, rr[j], dh, dlo, ac[j].x / (v.sig * v.sig + (float)y), rr + j, ac + j);
+        chi += apply_update(v, rr[j], dh, dlo, ac[j].x / (v.sig * v.sig + (float)y), rr + j, ac + j, st.handover_h);
     }
     const double chid = warp_sum((double)chi);
     if (lane == 0) {
@@ -519,6 +520,28 @@ __global__ void __launch_bounds__(256) k_mix_correct(DevGeo G, int64_t n_obs, fl
         pair_add(R.x, R.y, dc.x, dc.y);
         pair_add(R.x, R.y, corr, 0.0f);
         mr[o] = R;
+    }
+}
+
+// Block Gauss-Seidel (Sect. 4.6, Eq. precond): before the C block the (W, W R) pairs take
+// this iteration's attitude update d_att to first order, W R += W sum_j B_j g . d_a[l-3+j]
+__global__ void __launch_bounds__(256) k_mix_ac_correct(DevGeo G, int64_t n_obs, float2* __restrict__ mac,
+                                                        const MixT* __restrict__ mt,
+                                                        const float4* __restrict__ d_att) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
+        const MixT r = mt[o];
+        float B[4];
+        bspline4_lu(G, r.l, r.u, B);
+        const float4* da = d_att + (r.l - 3);
+        float corr = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float4 v = __ldg(da + j);
+            corr = fmaf(B[j], r.g[0] * v.x + r.g[1] * v.y + r.g[2] * v.z + r.g[3] * v.w, corr);
+        }
+        float2 a = mac[o];
+        a.y = fmaf(a.x, corr, a.y);
+        mac[o] = a;
     }
 }
 
@@ -713,7 +736,7 @@ __global__ void __launch_bounds__(32 * kW) k_mix_final(Settings st, const int64_
             arow(v, A);
             const int cls = v.sig < 0.0f ? 1 : 0;
             const float wgt = round_weight(in, R.x, R.x - adot(A, in.dp), cls, st.weight_fn);
-            chi += apply_update(v, R, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]), rr + jj, ac + jj);
+            chi += apply_update(v, R, f.dh, f.dl, wgt * (cls ? f.iw[1] : f.iw[0]), rr + jj, ac + jj, st.handover_h);
         };
         int j = lane;
         for (; j + kWarp < n; j += 2 * kWarp) {
@@ -1113,6 +1136,11 @@ void launch_mix_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t
     k_mix_cal_accum<<<grid_of(n_cal, sh.cal_threads / 32, 152 * sh.cal_bps), sh.cal_threads, 0, s>>>(
         n_cal, perm_c, cal_off, mo.ac, dtil, rd);
     k_mix_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal, d_cal);
+}
+
+void launch_mix_ac_correct(const DevGeo& G, int64_t n_obs, const MixObs& mo, const float* d_att, cudaStream_t s) {
+    k_mix_ac_correct<<<grid_of(n_obs, 256, 152 * 32), 256, 0, s>>>(G, n_obs, mo.ac, mo.t,
+                                                                    reinterpret_cast<const float4*>(d_att));
 }
 
 void launch_mix_prop(int32_t n_src, const int64_t* src_off, const MixObs& mo, const double* corr, cudaStream_t s) {

@@ -317,7 +317,7 @@ __device__ __noinline__ void solve_general(const Settings& st, int i, int64_t o0
         double R = e[0] - (e[1] * d[0] + e[2] * d[1] + e[3] * d[2] + e[4] * d[3] + e[5] * d[4]);
         double W = e[6] / (e[7] + y);
         ObsRec* r = rec + (o0 + j);
-        r->R = R;
+        r->R = st.handover_h ? e[0] : R;
         r->W = W;
         chi += W * R * R;
     }
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                 const double R = e[0] - (e[1] * dk[0] + e[2] * dk[1] + e[3] * dk[2] + e[4] * dk[3] + e[5] * dk[4]);
                 const double W = e[6] * (j < nal ? iw[0] : iw[1]);
                 ObsRec* r = rec + (o0 + j);
-                r->R = R;
+                r->R = st.handover_h ? e[0] : R;
                 r->W = W;
                 chi += W * R * R;
             }
