@@ -24,7 +24,7 @@ void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta,
                      double* R, cudaStream_t stream);
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
                       int n_iv, const ObsRec* rec, const double* att, double* blk, const Shapes& sh, cudaStream_t s);
-void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
+void launch_att_solve(int n_seg, int max_seg_knots, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
                       double* dx, cudaStream_t s);
@@ -254,6 +254,7 @@ struct agis_ctx {
     int n_iv = 0;
     double* blk = nullptr;
     int n_seg = 0;
+    int max_seg_knots = 0;   // the largest segment's coefficients (band rows / 4)
     int64_t n_rows = 0;
     int64_t* seg_row = nullptr;
     int32_t *seg_l = nullptr, *seg_n = nullptr, *seg_u = nullptr;
@@ -488,7 +489,7 @@ void enqueue_a(agis_ctx* c) {
     else
         launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
                          c->rec, c->att, c->blk, c->sh, c->stream);
-    launch_att_solve(c->n_seg, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
+    launch_att_solve(c->n_seg, c->max_seg_knots, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
                      c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->mixed ? c->d_att : nullptr,
                      c->datt64, c->stream);
     launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
@@ -882,6 +883,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         build_segments(n_coef, cfg->seg_len, cfg->seg_overlap, sl, sn, su, srow);
         c->n_seg = (int)(srow.size() - 1);
         c->n_rows = srow.back();
+        for (size_t q = 0; q + 1 < srow.size(); q++)
+            c->max_seg_knots = std::max(c->max_seg_knots, (int)((srow[q + 1] - srow[q]) / 4));
         if ((rc = dalloc(c, &c->seg_row, srow.size())) || (rc = dalloc(c, &c->seg_l, sl.size())) ||
             (rc = dalloc(c, &c->seg_n, sn.size())) || (rc = dalloc(c, &c->seg_u, su.size())) ||
             (rc = dalloc(c, &c->blk, (size_t)c->n_iv * kBlkVals)) || (rc = dalloc(c, &c->bandc, 16 * (size_t)c->n_rows)) ||

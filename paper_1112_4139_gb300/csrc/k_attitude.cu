@@ -123,46 +123,69 @@ __global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int
 }
 
 // Band of every segment in column layout: bandc[(row0 + c)*16 + k] = N[c-k][c] (k = 0..15)
-// and rhs[row0 + c], summed over the knot intervals of the segment only.
-__global__ void k_att_assemble(int n_seg, const int64_t* __restrict__ seg_row, const int32_t* __restrict__ seg_l,
-                               const int32_t* __restrict__ seg_n, const double* __restrict__ blk,
-                               double* __restrict__ bandc, double* __restrict__ rhs) {
-    const int64_t total = seg_row[n_seg] * 16;
-    const int64_t avg_rows = (seg_row[n_seg] + n_seg - 1) / n_seg > 0 ? (seg_row[n_seg] + n_seg - 1) / n_seg : 1;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = t >> 4;
-        const int k = (int)(t & 15);
-        // the segment of this row: the segments are of nearly equal length, so a guess from
-        // the average length and a step or two of correction replace a binary search
-        int sg = (int)(row / avg_rows);
-        if (sg > n_seg - 1) sg = n_seg - 1;
-        while (sg > 0 && seg_row[sg] > row) sg--;
-        while (sg < n_seg - 1 && seg_row[sg + 1] <= row) sg++;
-        const int c = (int)(row - seg_row[sg]);
+// and rhs[row0 + c], summed over the knot intervals of the segment only.  One warp per run of
+// kAsmKnots consecutive knots of a segment: the interval blocks those knots touch (a
+// contiguous range of blk) are copied into shared memory once, coalesced, and every band
+// entry of the run is summed from there over its intervals in increasing order.
+constexpr int kAsmKnots = 8;
+constexpr int kAsmWarps = 4;
+__global__ void __launch_bounds__(32 * kAsmWarps) k_att_assemble(int n_seg, int runs_per_seg,
+                                                                 const int64_t* __restrict__ seg_row,
+                                                                 const int32_t* __restrict__ seg_l,
+                                                                 const int32_t* __restrict__ seg_n,
+                                                                 const double* __restrict__ blk,
+                                                                 double* __restrict__ bandc, double* __restrict__ rhs) {
+    __shared__ double stage_all[kAsmWarps][(kAsmKnots + 3) * kBlkVals];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    double* st = stage_all[wib];
+    const int64_t n_units = (int64_t)n_seg * runs_per_seg;
+    for (int64_t u = (int64_t)blockIdx.x * kAsmWarps + wib; u < n_units; u += (int64_t)gridDim.x * kAsmWarps) {
+        const int sg = (int)(u / runs_per_seg);
+        const int run = (int)(u % runs_per_seg);
+        const int64_t row0 = seg_row[sg];
+        const int n_knots = (int)((seg_row[sg + 1] - row0) / 4);
+        const int k0 = run * kAsmKnots;
+        if (k0 >= n_knots) continue;
+        const int k1 = min(k0 + kAsmKnots, n_knots);
         const int l_lo = seg_l[2 * sg], l_hi = seg_l[2 * sg + 1];
         const int n_lo = seg_n[2 * sg];
-        const int v = c - k;
-        double val = 0.0;
-        if (v >= 0) {
-            const int nc = n_lo + (c >> 2), cc = c & 3;
-            const int nv = n_lo + (v >> 2), cv = v & 3;
-            int lb = nc > nv ? nc : nv;
-            int le = (nc < nv ? nc : nv) + 3;
-            if (lb < l_lo) lb = l_lo;
-            if (le > l_hi) le = l_hi;
-            for (int l = lb; l <= le; l++) {
-                const int i = 4 * (nv - l + 3) + cv, j = 4 * (nc - l + 3) + cc;
-                val += blk[(int64_t)(l - 3) * kBlkVals + tri16(i, j)];
-            }
+        // intervals touched by the knots n_lo + k0 .. n_lo + k1 - 1 (l = n .. n + 3), within the segment
+        const int lmin = max(n_lo + k0, l_lo), lmax = min(n_lo + k1 - 1 + 3, l_hi);
+        const int nb = lmax - lmin + 1;
+        __syncwarp();
+        if (nb > 0) {
+            const double* src = blk + (int64_t)(lmin - 3) * kBlkVals;
+            for (int e = lane; e < nb * kBlkVals; e += kWarp) st[e] = src[e];
         }
-        bandc[t] = val;
-        if (k == 0) {
+        __syncwarp();
+        const int n_ent = (k1 - k0) * 4 * 16;
+        for (int e = lane; e < n_ent; e += kWarp) {
+            const int c = 4 * k0 + (e >> 4);
+            const int k = e & 15;
+            const int v = c - k;
+            double val = 0.0;
+            if (v >= 0) {
+                const int nc = n_lo + (c >> 2), cc = c & 3;
+                const int nv = n_lo + (v >> 2), cv = v & 3;
+                int lb = nc > nv ? nc : nv;
+                int le = (nc < nv ? nc : nv) + 3;
+                if (lb < l_lo) lb = l_lo;
+                if (le > l_hi) le = l_hi;
+                for (int l = lb; l <= le; l++) {
+                    const int i = 4 * (nv - l + 3) + cv, j = 4 * (nc - l + 3) + cc;
+                    val += st[(l - lmin) * kBlkVals + tri16(i, j)];
+                }
+            }
+            bandc[(row0 + c) * 16 + k] = val;
+        }
+        for (int c = 4 * k0 + lane; c < 4 * k1; c += kWarp) {
             const int nc = n_lo + (c >> 2), cc = c & 3;
             double r = 0.0;
             int lb = nc < l_lo ? l_lo : nc;
             int le = nc + 3 > l_hi ? l_hi : nc + 3;
-            for (int l = lb; l <= le; l++) r += blk[(int64_t)(l - 3) * kBlkVals + 136 + 4 * (nc - l + 3) + cc];
-            rhs[row] = r;
+            for (int l = lb; l <= le; l++) r += st[(l - lmin) * kBlkVals + 136 + 4 * (nc - l + 3) + cc];
+            rhs[row0 + c] = r;
         }
     }
 }
@@ -186,7 +209,8 @@ constexpr int kSegsPerWarp = kWarp / kSegLanes;
 constexpr int kSolveSegWarps = 2;
 constexpr int kColAhead = 8;
 struct __align__(16) SegWin {
-    double W[16][16];            // W[row mod 16][col mod 16], upper part (row <= col) in use
+    double Wf[256];              // W[row mod 16][col mod 16] at row * 16 + (col + row) mod 16 (a
+                                 // diagonal skew: a column's entries fall in distinct banks)
     double z[16];                // partly reduced right-hand side per row slot
     double dg[16];               // original diagonal per row slot (the pivot test of C.1)
     double U[16];                // the current row of V: U[b] = V_{r, r+b} (b >= 1)
@@ -226,6 +250,10 @@ __device__ __forceinline__ double rcp_pos(double d) {
     return y;
 }
 
+__device__ __forceinline__ double& win(SegWin& sm, int row, int col) {
+    return sm.Wf[row * 16 + ((col + row) & 15)];
+}
+
 __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, const int64_t* __restrict__ seg_row,
                                                   const double* __restrict__ bandc, const double* __restrict__ rhs,
                                                   double* __restrict__ urow, double* __restrict__ yv,
@@ -263,7 +291,7 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
     for (int h = 0; h < 2; h++) {
         const int b = 2 * sub + h;
         for (int a = 0; a < 16; a++)
-            sm.W[a][b] = (a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
+            win(sm, a, b) = (a <= b && b < n) ? bandc[(base + b) * 16 + (b - a)] : 0.0;
         sm.dg[b] = b < n ? bandc[(base + b) * 16] : 0.0;
         sm.z[b] = b < n ? rhs[base + b] : 0.0;
     }
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
     for (int64_t r = 0; r < n_max; r++) {
         const bool live = r < n;
         const int s0 = (int)(r & 15);
-        const double piv = sm.W[s0][s0];
+        const double piv = win(sm, s0, s0);
         const double dg0 = sm.dg[s0];
         // the pivot test of Algorithm C.1; a failing pivot zeroes the row (rank defect)
         const bool pos = piv > tol * dg0;
@@ -297,7 +325,7 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
             const int b = sub + 1 + kSegLanes * h;
             if (b <= 15) {
                 const int sb = (int)((r + b) & 15);
-                double v = sm.W[s0][sb] * invd;
+                double v = win(sm, s0, sb) * invd;
                 if (r + b >= n) v = 0.0;
                 sm.U[b] = v;
                 sm.z[sb] -= v * wr;
@@ -315,8 +343,8 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
         for (int t = 0; t < 15; t++) {
             const int a = pa[t], b = pb[t];
             const int sb = (int)((r + b) & 15);
-            double& w = sm.W[(r + a) & 15][sb];
-            w -= sm.U[a] * sm.W[s0][sb];
+            double& w = win(sm, (int)((r + a) & 15), sb);
+            w -= sm.U[a] * win(sm, s0, sb);
         }
         // the column r + 16 enters in the slot of column r (row r's entries are no longer read)
         cp_async_wait_att<kColAhead - 1>();
@@ -326,7 +354,7 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
         for (int h = 0; h < 2; h++) {
             const int k = 2 * sub + h;   // band entry N[c - k][c]: window row a = 15 - k
             const int a = 15 - k;
-            sm.W[(r + 1 + a) & 15][s0] = c < n ? sm.ring[q][k] : 0.0;
+            win(sm, (int)((r + 1 + a) & 15), s0) = c < n ? sm.ring[q][k] : 0.0;
         }
         if (sub == 0) {
             sm.dg[s0] = c < n ? sm.ring[q][0] : 0.0;
@@ -401,15 +429,17 @@ void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint3
 }
 
 // d_att (mixed form only, else null) accumulates the applied update in FP32
-void launch_att_solve(int n_seg, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
+void launch_att_solve(int n_seg, int max_seg_knots, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
                       double* dx, cudaStream_t s) {
-    int64_t total = n_rows * 16;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    // knot runs per segment, enough for the largest segment
+    const int runs_per_seg = (max_seg_knots + kAsmKnots - 1) / kAsmKnots;
+    int64_t units = (int64_t)n_seg * runs_per_seg;
+    int blocks = (int)((units + kAsmWarps - 1) / kAsmWarps);
+    if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_att_assemble<<<blocks, 256, 0, s>>>(n_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
+    k_att_assemble<<<blocks, 32 * kAsmWarps, 0, s>>>(n_seg, runs_per_seg, seg_row, seg_l, seg_n, blk, bandc, rhs);
     const int seg_warps = (n_seg + kSegsPerWarp - 1) / kSegsPerWarp;
     k_att_solve<<<(seg_warps + kSolveSegWarps - 1) / kSolveSegWarps, 32 * kSolveSegWarps, 0, s>>>(
         n_seg, seg_row, bandc, rhs, urow, yv, x, tol, seg_rd);
