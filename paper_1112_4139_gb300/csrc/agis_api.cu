@@ -279,6 +279,7 @@ struct agis_ctx {
     double* hstat = nullptr;      // 10 S, 6 frame at 16, 4 ASI estimate at 24
     long long* hisum = nullptr;   // 2
     bool have_s = false;
+    bool a_since_c = false;     // an A update not yet seen by a C update (block Gauss-Seidel)
     static constexpr int kEvents = 14;
     cudaEvent_t ev[kEvents];
     double ktimes[5] = {0, 0, 0, 0, 0};
@@ -494,9 +495,10 @@ void enqueue_a(agis_ctx* c) {
                      c->datt64, c->stream);
     launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
 }
-void enqueue_c(agis_ctx* c) {
-    // block Gauss-Seidel (Eq. precond): the residuals C reads take the attitude update
-    if (c->cfg.block_order == 1) {
+void enqueue_c(agis_ctx* c, bool with_att = true) {
+    // block Gauss-Seidel (Eq. precond): the residuals C reads take the attitude update (once
+    // per A update: a repeated manual C update does not add it again)
+    if (c->cfg.block_order == 1 && with_att) {
         if (c->mixed)
             launch_mix_ac_correct(c->G, c->n_obs, c->mo, c->d_att, c->stream);
         else
@@ -921,6 +923,7 @@ int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     s_done(c, refresh);
     c->hist_count++;
     c->have_s = true;
+    c->a_since_c = false;   // the source update reset the attitude update C would see
     fill_s_stats(c, c->hstat, out);
     c->ktimes[0] = elapsed(c, 0, 1);
     if (out) {
@@ -937,6 +940,7 @@ int agis_attitude_update(agis_ctx* c, agis_block_stats* out) {
     if (!c->have_s) return fail(c, AGIS_E_INVALID, "attitude update needs a source update first");
     record(c, 2);
     enqueue_a(c);
+    c->a_since_c = true;
     record(c, 3);
     AGIS_CU(c, cudaMemcpyAsync(c->hisum, c->isum, sizeof(long long), cudaMemcpyDeviceToHost, c->stream), "stats");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "attitude update");
@@ -954,7 +958,8 @@ int agis_calibration_update(agis_ctx* c, agis_block_stats* out) {
     if (!c) return AGIS_E_INVALID;
     if (!c->have_s) return fail(c, AGIS_E_INVALID, "calibration update needs a source update first");
     record(c, 4);
-    enqueue_c(c);
+    enqueue_c(c, c->a_since_c);
+    c->a_since_c = false;
     record(c, 5);
     AGIS_CU(c, cudaMemcpyAsync(c->hisum + 1, c->isum + 1, sizeof(long long), cudaMemcpyDeviceToHost, c->stream),
             "stats");
@@ -1134,6 +1139,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
                     "stats");
         AGIS_CU(c, cudaStreamSynchronize(c->stream), "iteration");
         if (mask & 1) c->have_s = !do_frame;
+        c->a_since_c = false;
         if (per_iter) {
             agis_iter_stats& it = per_iter[k];
             std::memset(&it, 0, sizeof(it));
