@@ -18,6 +18,7 @@ Modules and the passages they follow:
   blocks    Sects. 5.1-5.3 and 6.1 (S, A, C blocks and the frame rotator)
   agis      Sect. 4.6 (the S[ACG] simple iteration)
   asi       Sect. 4.7 (the accelerated simple iteration)
+  attnoise  Sect. 5.2.5 (the excess attitude noise, Eqs. excess, W, wl, e09)
   mlp       the learned iteration proposal (not in the paper; analogue of the
             accelerated simple iteration of Sect. 4.7): network, loss, gradient,
             Adam, features and targets

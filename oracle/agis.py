@@ -4,6 +4,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import attnoise as AN
 from . import blocks as B
 from . import model as M
 
@@ -13,9 +14,11 @@ class State:
     src: np.ndarray   # [n_src, 5]
     att: np.ndarray   # [n_coef, 4]
     cal: np.ndarray   # [n_cal]
+    eps2_a: np.ndarray = None   # excess attitude noise [3, n_buckets] (Sect. 5.2.5), or None
 
     def copy(self):
-        return State(self.src.copy(), self.att.copy(), self.cal.copy())
+        return State(self.src.copy(), self.att.copy(), self.cal.copy(),
+                     None if self.eps2_a is None else self.eps2_a.copy())
 
 
 @dataclass
@@ -37,7 +40,22 @@ def iterate_once(P, state, st, ref=None, after_s=None):
     st.block_order selects the variants of Sect. 4.6 (see blocks.Settings).
     after_s(src1, sres, ev) -> (src1, R), if given, changes the sources after the S block and
     returns the residuals the A and C blocks read (the accelerated iteration, Sect. 4.7)."""
-    src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st)
+    an = st.att_noise_bucket_ns > 0
+    if an:
+        # excess attitude noise (Sect. 5.2.5): the source update with sigma~^2 = sigma^2 +
+        # eps_a^2 of the previous estimate (Eq. W), then eps_a^2 from its residuals (Eq. e09)
+        sig2 = P.sigma.astype(np.float64) ** 2
+        comp = AN.component(P.kind, P.fov)
+        bucket = AN.bucket_of(P.t_ns, P.knot0_ns, st.att_noise_bucket_ns)
+        n_b = int(bucket.max()) + 1
+        eps2_a = state.eps2_a if state.eps2_a is not None else np.zeros((AN.N_COMP, n_b))
+        src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st,
+                                         sig2=AN.adjusted_variance(sig2, eps2_a, comp, bucket))
+        eps2_i_obs = sres.eps2[P.src]
+        eps2_a = AN.estimate(sres.R, sig2, eps2_i_obs, comp, bucket, n_b)
+        W_att = AN.attitude_weights(sres.R, sig2, eps2_i_obs, eps2_a, comp, bucket, B._wfun(st))
+    else:
+        src1, sres, ev = B.source_update(P, state.src, state.att, state.cal, st)
     R = sres.R
     if after_s is not None:
         src1, R = after_s(src1, sres, ev)
@@ -46,7 +64,7 @@ def iterate_once(P, state, st, ref=None, after_s=None):
     att1, rda = state.att.copy(), 0
     cal1, rdc = state.cal.copy(), 0
     if "A" in st.block_mask:
-        att1, rda = B.attitude_update(P, state.att, ev, R, sres.W, st)
+        att1, rda = B.attitude_update(P, state.att, ev, R, W_att if an else sres.W, st)
     Rc = R
     if st.block_order == "SAC":
         # Gauss-Seidel: C sees the attitude update through the linearised residuals,
@@ -67,7 +85,7 @@ def iterate_once(P, state, st, ref=None, after_s=None):
         chi2=float(np.sum(sres.W * sres.R ** 2)), Q=float(np.sum(sres.Qi)), nu=int(np.sum(sres.nu)),
         n_out=int(np.sum(sres.n_out)), rank_def_s=int(np.sum(sres.rank_def)), rank_def_a=int(rda),
         rank_def_c=int(rdc), frame=frame, d_rms=np.sqrt(np.mean(sres.d ** 2, axis=0)))
-    return State(src1, att1, cal1), stats, sres
+    return State(src1, att1, cal1, eps2_a if an else state.eps2_a), stats, sres
 
 
 def iterate(P, state, st, n_iter, ref=None, callback=None):

@@ -57,6 +57,8 @@ class Settings:
     # (Gauss-Seidel, Eq. precond); "[SAC]" A and C from the residuals before the source
     # update (Jacobi, Eq. precond(SCAG))
     block_order: str = "S[AC]"
+    # excess attitude noise (Sect. 5.2.5): bucket length in ns, 0 = not estimated
+    att_noise_bucket_ns: int = 0
 
 
 def _wfun(st):
@@ -143,9 +145,11 @@ def source_update_one(A, h, sig2, st):
     return dict(d=d, eps2=y, R=R, W=w / (sig2 + y), Qi=Qy, nu=nu, n_out=n_out, D=D, U=U, rd=rd)
 
 
-def source_update(P, src, att, cal, st, ev=None):
+def source_update(P, src, att, cal, st, ev=None, sig2=None):
     """S block: per-source 5x5 solves (Eq. normS) and the parameter update (footnote to
-    Eq. ubardiff: alpha += d0 / cos(delta)).  Returns (new sources, SourceResult, ev)."""
+    Eq. ubardiff: alpha += d0 / cos(delta)).  sig2: the observation variances to use (default
+    sigma_l^2; sigma~_l^2 with the excess attitude noise, Eq. W).  Returns (new sources,
+    SourceResult, ev)."""
     if ev is None:
         ev = M.evaluate(P, src, att, cal)
     off = P.src_offsets()
@@ -153,7 +157,8 @@ def source_update(P, src, att, cal, st, ev=None):
     res = SourceResult(d=np.zeros((ns, 5)), eps2=np.zeros(ns), Qi=np.zeros(ns), nu=np.zeros(ns, np.int64),
                        n_out=np.zeros(ns, np.int64), D=np.zeros(ns), cov=np.zeros((ns, 5, 5)),
                        rank_def=np.zeros(ns, np.int64), R=np.zeros(P.n_obs), W=np.zeros(P.n_obs))
-    sig2 = P.sigma.astype(np.float64) ** 2
+    if sig2 is None:
+        sig2 = P.sigma.astype(np.float64) ** 2
     for i in range(ns):
         a, b = off[i], off[i + 1]
         if b == a:
