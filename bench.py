@@ -32,13 +32,14 @@ WORKLOADS = {
     "uneven5yr": "3M sources, 5 yr, 30-s knots, G ~ U(12, 18) with sigma_AL 50-500 uas, 40-250 transits",
 }
 # kernels launched by one iteration, (with a full FP64 evaluation, with the linearized pass):
-# FP64 form: S (source geometry, observation pass, per-source solve, stats), A (accumulate,
-# assemble, solve, apply, rank-defect sum), C (accumulate, project, rank-defect sum), frame
-# (normals, solve, apply sources, apply attitude) = 16.  Mixed form: the S pass is source
-# geometry + full evaluation, or the one linearized-correction kernel; the S solves are
-# scale/round-0 sums, 5 rounds of 5x5 algebra, 4 rounds of sums, final pass, per-observation
-# path, stats = 13 (default 4 reweighting rounds); A, C and frame as above.
-KERNELS_PER_STEP = {"fp64": (16, 16), "mixed": (2 + 13 + 12, 1 + 13 + 12)}
+# FP64 form: S (source geometry, observation pass, per-source solve, stats in two stages,
+# update-history push), A (accumulate, assemble, solve, apply, rank-defect sum), C
+# (accumulate, project, rank-defect sum), frame (normals, solve, apply sources, apply
+# attitude) = 18.  Mixed form: the S pass is source geometry + full evaluation, or the one
+# linearized-correction kernel; the S solves are scale/round-0 sums, 5 rounds of 5x5 algebra,
+# 4 rounds of sums, final pass, per-observation path, stats (two), history push = 15 (default
+# 4 reweighting rounds); A, C and frame as above.
+KERNELS_PER_STEP = {"fp64": (18, 18), "mixed": (2 + 15 + 12, 1 + 15 + 12)}
 FP64_PEAK_TFLOPS = 1.25
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per observation of the linearized observation pass (see time_form)

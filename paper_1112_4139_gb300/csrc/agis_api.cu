@@ -59,7 +59,7 @@ void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* ca
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
                   double* att, double* partial, int n_part, double tol, double* eo, cudaStream_t s);
 void launch_src_stats(int n_src, const double* chi2, const double* q, const int* nu, const int* nout, const int* rdf,
-                      const double* d, double* out, cudaStream_t s);
+                      const double* d, double* out, double* part, cudaStream_t s);
 void launch_int_sum(int n, const int* v, long long* out, cudaStream_t s);
 }  // namespace agis
 
@@ -248,6 +248,7 @@ struct agis_ctx {
     int* work = nullptr;
     SrcOutPtrs so{};
     double* sstats = nullptr;     // 10
+    double* sstat_part = nullptr; // 304 x 10 partial sums of the source statistics
     // A block
     uint32_t* perm_t = nullptr;
     int64_t* ivl_off = nullptr;
@@ -455,7 +456,7 @@ void enqueue_s_solve(agis_ctx* c) {
         launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
                             c->work, c->n_sblocks, c->sh, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
-                     c->stream);
+                     c->sstat_part, c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
     // block Gauss-Seidel, FP64 form: the attitude update C will see is this iteration's (none
     // until an A block runs)
@@ -873,7 +874,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         (rc = dalloc(c, &c->so.dsig, n_src)) || (rc = dalloc(c, &c->so.chi2, n_src)) ||
         (rc = dalloc(c, &c->so.cov, 25 * (size_t)n_src)) || (rc = dalloc(c, &c->so.nu, n_src)) ||
         (rc = dalloc(c, &c->so.nout, n_src)) || (rc = dalloc(c, &c->so.rankdef, n_src)) ||
-        (rc = dalloc(c, &c->sstats, 16)))
+        (rc = dalloc(c, &c->sstats, 16)) || (rc = dalloc(c, &c->sstat_part, 512 * 10)))
         return bail(rc);
     c->so.src = c->src;
     if ((rc = dalloc(c, &c->hist, 20 * (size_t)n_src))) return bail(rc);

@@ -274,16 +274,26 @@ void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, doub
 }
 
 // ---------------------------------------------------------------------------------------
-// Deterministic statistics of the S block: one block, fixed strided order then a tree.
+// Deterministic statistics of the S block, in two stages.
 // out: [chi2, q, nu, nout, rankdef, d2 x5]
 // ---------------------------------------------------------------------------------------
-__global__ void k_src_stats(int n_src, const double* __restrict__ chi2, const double* __restrict__ q,
-                            const int* __restrict__ nu, const int* __restrict__ nout, const int* __restrict__ rdf,
-                            const double* __restrict__ d, double* __restrict__ out) {
-    __shared__ double sh[1024];
+// Stage 1: block b reduces the sources of its fixed contiguous chunk into part[b][10];
+// stage 2 (one block) adds the parts in block order, so the sums do not depend on timing.
+constexpr int kStatBlocks = 304;
+constexpr int kStatThreads = 256;
+__global__ void __launch_bounds__(kStatThreads) k_src_stats_part(int n_src, const double* __restrict__ chi2,
+                                                                 const double* __restrict__ q,
+                                                                 const int* __restrict__ nu,
+                                                                 const int* __restrict__ nout,
+                                                                 const int* __restrict__ rdf,
+                                                                 const double* __restrict__ d,
+                                                                 double* __restrict__ part) {
+    __shared__ double sh[kStatThreads];
+    const int chunk = (n_src + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * chunk, hi = min(n_src, lo + chunk);
     double acc[10];
     for (int k = 0; k < 10; k++) acc[k] = 0.0;
-    for (int i = threadIdx.x; i < n_src; i += blockDim.x) {
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         acc[0] += chi2[i];
         acc[1] += q[i];
         acc[2] += (double)nu[i];
@@ -298,8 +308,17 @@ __global__ void k_src_stats(int n_src, const double* __restrict__ chi2, const do
             if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) out[k] = sh[0];
+        if (threadIdx.x == 0) part[blockIdx.x * 10 + k] = sh[0];
         __syncthreads();
+    }
+}
+__global__ void __launch_bounds__(32) k_src_stats_final(int n_part, const double* __restrict__ part,
+                                                        double* __restrict__ out) {
+    // lane k < 10 adds statistic k over the parts in order
+    if (threadIdx.x < 10) {
+        double a = 0.0;
+        for (int b = 0; b < n_part; b++) a += part[b * 10 + threadIdx.x];
+        out[threadIdx.x] = a;
     }
 }
 
@@ -317,9 +336,11 @@ __global__ void k_int_sum(int n, const int* __restrict__ v, long long* __restric
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// out: 10 sums; part: kStatBlocks x 10 doubles of scratch
 void launch_src_stats(int n_src, const double* chi2, const double* q, const int* nu, const int* nout, const int* rdf,
-                      const double* d, double* out, cudaStream_t s) {
-    k_src_stats<<<1, 1024, 0, s>>>(n_src, chi2, q, nu, nout, rdf, d, out);
+                      const double* d, double* out, double* part, cudaStream_t s) {
+    k_src_stats_part<<<kStatBlocks, kStatThreads, 0, s>>>(n_src, chi2, q, nu, nout, rdf, d, part);
+    k_src_stats_final<<<1, 32, 0, s>>>(kStatBlocks, part, out);
 }
 
 void launch_int_sum(int n, const int* v, long long* out, cudaStream_t s) { k_int_sum<<<1, 1024, 0, s>>>(n, v, out); }
