@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 6
+#define AGIS_ABI_VERSION 7
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -328,6 +328,38 @@ int agis_set_asi(agis_ctx* ctx, int32_t stride, double lambda_max);
  * AGIS_E_CUDA. */
 int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, int32_t stride, double lambda_max,
                       void* scratch, double* est, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Excess attitude noise (Sect. 5.2.5, Eqs. excess, W, wl, e09)
+ *
+ * The excess noise of an observation is modelled as eps_i^2 (its source, estimated by the
+ * source update) plus eps_a^2(t), one function of time per component: AL, AC in the
+ * preceding field of view (fov 0) and AC in the following one (fov 1).  Each is constant on
+ * buckets [knot0_ns + j bucket_ns, knot0_ns + (j+1) bucket_ns), j = 0 .. n_buckets - 1,
+ * n_buckets reaching the last observation.  With the noise on, every source update (in
+ * agis_iterate and agis_source_update):
+ *   uses sigma~^2 = sigma^2 + eps_a^2(t) in place of sigma^2 (robust scale, weights and
+ *             normals; Eq. W), eps_a^2 being the estimate of the previous source update
+ *             (0 after this call);
+ *   estimates eps_a^2(j) = max(0, F_0.68{R_l^2 - sigma_l^2 - eps_i^2}) over the observations
+ *             l of bucket j and the component (Eq. e09; R the residual after the update,
+ *             sigma the formal one, F_0.68 the 68% quantile with linear interpolation between
+ *             order statistics, 0 for an empty bucket);
+ *   and the next attitude update weighs observation l with w(R_l / sqrt(v)) / v,
+ *             v = sigma_l^2 + eps_a^2(t_l) + eps_i^2 (Eqs. W, wl) in place of the weights of
+ *             the source update; the calibration update keeps the latter.
+ * bucket_ns > 0 switches the noise on (eps_a^2 = 0), 0 switches it off.  FP64 form only
+ * (precision 0), block orders S[AC] and SAC, not together with ASI or the learned proposal.
+ * Errors: AGIS_E_INVALID (bucket_ns < 0, one of those combinations, an observation before
+ * knot0_ns, more than 2^30 / 3 buckets), AGIS_E_OOM, AGIS_E_CUDA.  Device memory: 20 bytes
+ * per observation and 32 bytes per bucket, owned by the context. */
+int agis_set_attnoise(agis_ctx* ctx, int64_t bucket_ns);
+/* *n_buckets = the number of buckets (0 when the noise is off); if eps2_a is not NULL and
+ * the noise is on, eps2_a[c * n_buckets + j] = eps_a^2 of component c (0 AL, 1 AC preceding
+ * field, 2 AC following field) in bucket j, rad^2, from the last source update (host or
+ * device memory, 3 x n_buckets FP64, caller-owned).  Synchronous.  Errors: AGIS_E_INVALID
+ * (null ctx or n_buckets), AGIS_E_CUDA. */
+int agis_get_attnoise(agis_ctx* ctx, double* eps2_a, int32_t* n_buckets);
 
 /* ---------------------------------------------------------------------------------------
  * Launch-shape autotuner (iteration control)

@@ -19,7 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 6  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 7  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -28,7 +28,7 @@ EXPORTS = (
     "agis_abi_version", "agis_source_update_static", "agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad",
     "agis_mlp_adam", "agis_proposal_targets", "agis_set_proposal", "agis_get_proposal_features",
     "agis_copy_sources_device", "agis_set_asi", "agis_asi_estimate", "agis_autotune", "agis_get_tuning",
-    "agis_set_tuning",
+    "agis_set_tuning", "agis_set_attnoise", "agis_get_attnoise",
 )
 KNOBS = ("obs_pass", "src_batch", "mix_sums", "mix_solve5", "att_accum", "cal_accum")  # AGIS_KNOB_* order
 STATIC_MAX_OBS = 16384
@@ -140,9 +140,12 @@ def load():
         lib.agis_autotune.argtypes = [V, C.c_int32, C.POINTER(C.c_int32), P]
         lib.agis_get_tuning.argtypes = [V, P]
         lib.agis_set_tuning.argtypes = [V, P, C.c_int32]
+        lib.agis_set_attnoise.argtypes = [V, C.c_int64]
+        lib.agis_get_attnoise.argtypes = [V, P, C.POINTER(C.c_int32)]
         for f in ("agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad", "agis_mlp_adam", "agis_proposal_targets",
                   "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device", "agis_set_asi",
-                  "agis_asi_estimate", "agis_autotune", "agis_get_tuning", "agis_set_tuning"):
+                  "agis_asi_estimate", "agis_autotune", "agis_get_tuning", "agis_set_tuning", "agis_set_attnoise",
+                  "agis_get_attnoise"):
             getattr(lib, f).restype = I
         if lib.agis_abi_version() != ABI_VERSION:
             raise RuntimeError(f"libagis.so has ABI {lib.agis_abi_version()}, this binding {ABI_VERSION}: rebuild")
@@ -344,6 +347,22 @@ class Agis:
         """Extrapolate the source update of each iteration by 1/(1 - lambda), lambda from the
         parallax updates of every stride-th source; stride 0 disables."""
         self._check(self._lib.agis_set_asi(self.ctx, int(stride), float(lambda_max)))
+
+    # excess attitude noise
+    def set_attnoise(self, bucket_ns):
+        """Estimate the excess attitude noise on buckets of bucket_ns from knot0_ns; 0 disables."""
+        self._check(self._lib.agis_set_attnoise(self.ctx, int(bucket_ns)))
+
+    def attnoise(self):
+        """eps_a^2 [3, n_buckets] (AL, AC preceding field, AC following field) of the last
+        source update, or None when the noise is off."""
+        nb = C.c_int32(0)
+        self._check(self._lib.agis_get_attnoise(self.ctx, None, C.byref(nb)))
+        if nb.value == 0:
+            return None
+        out = np.empty((3, nb.value), dtype=np.float64)
+        self._check(self._lib.agis_get_attnoise(self.ctx, out.ctypes.data, C.byref(nb)))
+        return out
 
 
 def _mlp_call(name, *args):

@@ -12,7 +12,7 @@
 #include "agis_internal.cuh"
 
 namespace agis {
-void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+void launch_obs_pass(const DevGeo& G, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
                      const Shapes& sh, cudaStream_t stream);
@@ -23,7 +23,8 @@ void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
-                      int n_iv, const ObsRec* rec, const double* att, double* blk, const Shapes& sh, cudaStream_t s);
+                      int n_iv, const ObsRec* rec, const double* w_att, const double* att, double* blk,
+                      const Shapes& sh, cudaStream_t s);
 void launch_att_solve(int n_seg, int max_seg_knots, int n_coef, int64_t n_rows, const int64_t* seg_row, const int32_t* seg_l,
                       const int32_t* seg_n, const int32_t* seg_u, const double* blk, double* bandc, double* rhs,
                       double* urow, double* yv, double* x, double tol, int* seg_rd, double* att, float* d_att,
@@ -61,6 +62,12 @@ void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, doub
 void launch_src_stats(int n_src, const double* chi2, const double* q, const int* nu, const int* nout, const int* rdf,
                       const double* d, double* out, double* part, cudaStream_t s);
 void launch_int_sum(int n, const int* v, long long* out, cudaStream_t s);
+void launch_an_range(int64_t n, const int64_t* t, int64_t t0, unsigned long long* mx, int* neg, cudaStream_t s);
+void launch_an_keys(int64_t n, const int64_t* t, const uint32_t* meta, const AttNoise& an, int32_t* key, uint32_t* val,
+                    cudaStream_t s);
+void launch_an_estimate(int64_t n, const AttNoise& an, double* eps2, const uint32_t* perm, const int64_t* off,
+                        const ObsRec* rec, const float* sigma, const int32_t* obs_src, const double* eps2_src,
+                        int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s);
 }  // namespace agis
 
 using namespace agis;
@@ -312,6 +319,16 @@ struct agis_ctx {
     double asi_lam_max = 0.9;
     unsigned long long* asi_keys = nullptr;
     double* asi_est = nullptr;
+    // excess attitude noise (FP64 form; an.eps2 null: off): bucket length, eps_a^2 [3 x n_b],
+    // the (component, bucket) order and its run offsets, the x_l keys in that order, and the
+    // attitude weights (source order)
+    int64_t an_bucket_ns = 0;
+    AttNoise an;
+    double* an_eps2 = nullptr;
+    uint32_t* an_perm = nullptr;
+    int64_t* an_off = nullptr;
+    uint64_t* an_x = nullptr;
+    double* an_w = nullptr;
     // launch shapes (defaults until agis_autotune or agis_set_tuning)
     Shapes sh;
     bool graphs_ready = false;
@@ -342,6 +359,17 @@ int dalloc(agis_ctx* c, T** p, size_t count) {
     c->allocs.push_back(q);
     *p = (T*)q;
     return AGIS_OK;
+}
+
+// frees an array of dalloc before agis_destroy
+void dfree(agis_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); i++)
+        if (c->allocs[i] == p) {
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            cudaFree(p);
+            return;
+        }
 }
 
 // device temporary of the set-up, freed at the end of its scope
@@ -445,7 +473,7 @@ void enqueue_s_pass(agis_ctx* c, bool refresh) {
                         c->att, c->cal, c->mo, c->sgeo, c->d_att, c->d_cal, c->n_coef, c->n_cal, c->sh,
                         c->stream);
     else
-        launch_obs_pass(c->G, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
+        launch_obs_pass(c->G, c->an, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
                         c->cal, c->rec, c->sgeo, c->scratch, c->sh, c->stream);
 }
 void enqueue_s_solve(agis_ctx* c) {
@@ -455,6 +483,10 @@ void enqueue_s_solve(agis_ctx* c) {
     else
         launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
                             c->work, c->n_sblocks, c->sh, c->stream);
+    // excess attitude noise from the residuals of this source update, and the attitude weights
+    if (c->an.eps2)
+        launch_an_estimate(c->n_obs, c->an, c->an_eps2, c->an_perm, c->an_off, c->rec, c->sigma, c->obs_src,
+                           c->so.eps2, c->st.weight_fn, c->an_x, c->an_w, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->sstat_part, c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
@@ -490,7 +522,7 @@ void enqueue_a(agis_ctx* c) {
                              c->att, c->blk, c->sh, c->stream);
     else
         launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
-                         c->rec, c->att, c->blk, c->sh, c->stream);
+                         c->rec, c->an.eps2 ? c->an_w : nullptr, c->att, c->blk, c->sh, c->stream);
     launch_att_solve(c->n_seg, c->max_seg_knots, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
                      c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, c->mixed ? c->d_att : nullptr,
                      c->datt64, c->stream);
@@ -1255,6 +1287,7 @@ int agis_set_proposal(agis_ctx* c, const float* params, int32_t every) {
     if (every < 5) return fail(c, AGIS_E_INVALID, "proposal period below 5 iterations");
     if (c->cfg.block_order == 2)
         return fail(c, AGIS_E_INVALID, "the learned proposal needs block order S[AC] or SAC");
+    if (c->an.eps2) return fail(c, AGIS_E_INVALID, "the learned proposal does not combine with the excess attitude noise");
     if (!c->prop_packed) {
         void* packed = nullptr;
         AGIS_TRY(dalloc(c, reinterpret_cast<uint8_t**>(&packed), AGIS_MLP_PACKED_BYTES));
@@ -1291,6 +1324,7 @@ int agis_set_asi(agis_ctx* c, int32_t stride, double lambda_max) {
     }
     if (!(lambda_max >= 0.0 && lambda_max < 1.0)) return fail(c, AGIS_E_INVALID, "lambda_max outside [0, 1)");
     if (c->cfg.block_order == 2) return fail(c, AGIS_E_INVALID, "ASI needs block order S[AC] or SAC");
+    if (c->an.eps2) return fail(c, AGIS_E_INVALID, "ASI does not combine with the excess attitude noise");
     if (!c->asi_keys) {
         const size_t n_s = std::max<size_t>(1, ((size_t)c->n_src + stride - 1) / stride);
         AGIS_TRY(dalloc(c, &c->asi_keys, std::max<size_t>(n_s, (size_t)c->n_src)));
@@ -1300,6 +1334,92 @@ int agis_set_asi(agis_ctx* c, int32_t stride, double lambda_max) {
     c->asi_stride = stride;
     c->asi_lam_max = lambda_max;
     drop_graphs(c);   // the stride and the clamp are captured in the ASI graph
+    return AGIS_OK;
+}
+
+// --- excess attitude noise (Sect. 5.2.5) --------------------------------------------------
+
+int agis_set_attnoise(agis_ctx* c, int64_t bucket_ns) {
+    if (!c) return AGIS_E_INVALID;
+    if (bucket_ns < 0) return fail(c, AGIS_E_INVALID, "bucket_ns below 0");
+    if (bucket_ns > 0) {
+        if (c->mixed) return fail(c, AGIS_E_INVALID, "the excess attitude noise needs the FP64 form (precision 0)");
+        if (c->cfg.block_order == 2)
+            return fail(c, AGIS_E_INVALID, "the excess attitude noise needs block order S[AC] or SAC");
+        if (c->asi_stride > 0 || c->prop_every > 0)
+            return fail(c, AGIS_E_INVALID, "the excess attitude noise does not combine with ASI or the proposal");
+    }
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "set_attnoise (sync)");
+    drop_graphs(c);   // the estimate and the adjusted variances are captured in the graphs
+    dfree(c, c->an_eps2);
+    dfree(c, c->an_perm);
+    dfree(c, c->an_off);
+    dfree(c, c->an_x);
+    dfree(c, c->an_w);
+    c->an_eps2 = nullptr;
+    c->an_perm = nullptr;
+    c->an_off = nullptr;
+    c->an_x = nullptr;
+    c->an_w = nullptr;
+    c->an = AttNoise{};
+    c->an_bucket_ns = 0;
+    if (bucket_ns == 0 || c->n_obs == 0) return AGIS_OK;
+    const int64_t n = c->n_obs;
+    cudaStream_t s = c->stream;
+    // number of buckets from the last observation; none may precede the first bucket
+    int64_t n_b = 0;
+    {
+        TmpDev tm;
+        unsigned long long* mx = nullptr;
+        AGIS_TRY(tm.alloc(c, &mx, 2));
+        int* neg = reinterpret_cast<int*>(mx + 1);
+        AGIS_CU(c, cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), s), "set_attnoise (memset)");
+        launch_an_range(n, c->t_ns, c->G.knot0_ns, mx, neg, s);
+        unsigned long long h[2] = {0, 0};
+        AGIS_CU(c, cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, s), "set_attnoise (range)");
+        AGIS_CU(c, cudaStreamSynchronize(s), "set_attnoise (range sync)");
+        if (h[1] != 0ull)
+            return fail(c, AGIS_E_INVALID, "an observation precedes knot0_ns, the start of the first bucket");
+        n_b = (int64_t)(h[0] / (unsigned long long)bucket_ns) + 1;
+    }
+    if (3 * n_b >= (int64_t)1 << 30) return fail(c, AGIS_E_INVALID, "more than 2^30 / 3 attitude-noise buckets");
+    AttNoise an;
+    an.t0 = c->G.knot0_ns;
+    an.dt = bucket_ns;
+    an.n_b = (int32_t)n_b;
+    AGIS_TRY(dalloc(c, &c->an_eps2, 3 * (size_t)n_b));
+    AGIS_TRY(dalloc(c, &c->an_perm, (size_t)n));
+    AGIS_TRY(dalloc(c, &c->an_off, 3 * (size_t)n_b + 1));
+    AGIS_TRY(dalloc(c, &c->an_x, (size_t)n));
+    AGIS_TRY(dalloc(c, &c->an_w, (size_t)n));
+    AGIS_CU(c, cudaMemsetAsync(c->an_eps2, 0, sizeof(double) * 3 * (size_t)n_b, s), "set_attnoise (memset)");
+    {
+        TmpDev tk_in, tk_out, tv_in;
+        int32_t *k_in = nullptr, *k_out = nullptr;
+        uint32_t* v_in = nullptr;
+        AGIS_TRY(tk_in.alloc(c, &k_in, n));
+        AGIS_TRY(tk_out.alloc(c, &k_out, n));
+        AGIS_TRY(tv_in.alloc(c, &v_in, n));
+        launch_an_keys(n, c->t_ns, c->meta, an, k_in, v_in, s);
+        AGIS_TRY(sort_pairs(c, k_in, k_out, v_in, c->an_perm, n, bits_for(3 * n_b)));
+        k_lower_bound<int32_t><<<grid_for(3 * n_b + 1, 256), 256, 0, s>>>(k_out, n, 3 * n_b + 1, c->an_off);
+        AGIS_CU(c, cudaStreamSynchronize(s), "set_attnoise (order)");
+    }
+    an.eps2 = c->an_eps2;
+    c->an = an;
+    c->an_bucket_ns = bucket_ns;
+    return AGIS_OK;
+}
+
+int agis_get_attnoise(agis_ctx* c, double* eps2_a, int32_t* n_buckets) {
+    if (!c || !n_buckets) return AGIS_E_INVALID;
+    *n_buckets = c->an.n_b;
+    if (eps2_a && c->an.n_b > 0) {
+        AGIS_CU(c, cudaMemcpyAsync(eps2_a, c->an_eps2, sizeof(double) * 3 * (size_t)c->an.n_b, cudaMemcpyDeviceToHost,
+                                   c->stream),
+                "get_attnoise");
+        AGIS_CU(c, cudaStreamSynchronize(c->stream), "get_attnoise (sync)");
+    }
     return AGIS_OK;
 }
 

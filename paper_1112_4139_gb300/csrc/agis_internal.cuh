@@ -226,6 +226,29 @@ __device__ __forceinline__ double wfun(double z, int fn) {
 }
 
 // knot tau_k (ns) of the uniform sequence with 4-fold end knots
+// order-preserving map of an FP64 value to an unsigned key (and back), for radix selection
+__device__ __forceinline__ uint64_t dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b < 0 ? ~(uint64_t)b : ((uint64_t)b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(uint64_t k) {
+    long long b = (k & 0x8000000000000000ull) ? (long long)(k & 0x7fffffffffffffffull) : (long long)(~k);
+    return __longlong_as_double(b);
+}
+
+// Excess attitude noise (Sect. 5.2.5): eps_a^2 of the three components (AL, AC in the
+// preceding field, AC in the following field) per time bucket [t0 + j dt, t0 + (j+1) dt),
+// stored eps2[comp * n_b + j].  eps2 null: off.
+struct AttNoise {
+    const double* eps2 = nullptr;
+    int64_t t0 = 0, dt = 1;
+    int32_t n_b = 0;
+};
+__device__ __forceinline__ int an_comp(uint32_t m) { return meta_kind(m) == 0 ? 0 : 1 + (int)meta_fov(m); }
+__device__ __forceinline__ int64_t an_index(const AttNoise& a, int64_t t, uint32_t m) {
+    return (int64_t)an_comp(m) * a.n_b + (t - a.t0) / a.dt;   // t >= t0 (checked when switched on)
+}
+
 __device__ __forceinline__ int64_t knot_at(const DevGeo& G, int64_t k) {
     int64_t K = (int64_t)G.n_coef - 3;
     int64_t j = k - 3;

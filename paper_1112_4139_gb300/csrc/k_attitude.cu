@@ -19,12 +19,14 @@ constexpr int kAccFP64 = 116;  // distinct products: BB[p] M[m] (10 x 10) and B[
 // to the right-hand side -W B (x) (R g [- 2 lambda^2 D s]).  The 136 upper entries of the
 // block hold only 100 distinct products (the 10 upper entries of B B' times those of the
 // symmetric 4x4 M), so the lanes accumulate those 100 and the 16 right-hand-side products
-// (4 per lane) and expand them into the 152 outputs at the end.
+// (4 per lane) and expand them into the 152 outputs at the end.  W is the weight of the
+// source update, or w_att[o] (Eqs. W, wl) when the excess attitude noise is estimated.
 __global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int rhs_norm,
                                                    const uint32_t* __restrict__ perm_t,
                                                    const int64_t* __restrict__ ivl_off, int n_iv,
-                                                   const ObsRec* __restrict__ rec, const double* __restrict__ att,
-                                                   double* __restrict__ blk) {
+                                                   const ObsRec* __restrict__ rec,
+                                                   const double* __restrict__ w_att,
+                                                   const double* __restrict__ att, double* __restrict__ blk) {
     __shared__ double stage_all[4][kWarp * kStage];
     __shared__ double red_all[4][kAccFP64];
     __shared__ int16_t src_tab[kBlkVals];  // accumulator of each block output
@@ -69,13 +71,14 @@ __global__ void __launch_bounds__(128) k_att_accum(DevGeo G, double lambda2, int
             const int64_t j = base + lane;
             double* st = stg + lane * kStage;
             if (j < end) {
-                const ObsRec r = rec[perm_t[j]];
+                const uint32_t o = perm_t[j];
+                const ObsRec r = rec[o];
                 double B[4];
                 bspline4(G, r.t_ns, l, B);
                 double s[4];
 #pragma unroll
                 for (int c = 0; c < 4; c++) s[c] = B[0] * a[c] + B[1] * a[4 + c] + B[2] * a[8 + c] + B[3] * a[12 + c];
-                const double W = r.W;
+                const double W = w_att ? w_att[o] : r.W;
                 const double l4 = 4.0 * lambda2;
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
@@ -419,13 +422,14 @@ __global__ void k_att_apply(int n_coef, int n_seg, const int32_t* __restrict__ s
 }
 
 void launch_att_accum(const DevGeo& G, double lambda2, int rhs_norm, const uint32_t* perm_t, const int64_t* ivl_off,
-                      int n_iv, const ObsRec* rec, const double* att, double* blk, const Shapes& sh, cudaStream_t s) {
+                      int n_iv, const ObsRec* rec, const double* w_att, const double* att, double* blk,
+                      const Shapes& sh, cudaStream_t s) {
     int warps = n_iv;
     int blocks = (warps + 3) / 4;
     const int bps = sh.att_bps > 0 ? sh.att_bps : 32;
     if (blocks > 152 * bps) blocks = 152 * bps;
     if (blocks < 1) blocks = 1;
-    k_att_accum<<<blocks, 128, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, att, blk);
+    k_att_accum<<<blocks, 128, 0, s>>>(G, lambda2, rhs_norm, perm_t, ivl_off, n_iv, rec, w_att, att, blk);
 }
 
 // d_att (mixed form only, else null) accumulates the applied update in FP32

@@ -12,14 +12,6 @@
 namespace agis {
 
 
-__device__ __forceinline__ uint64_t dkey(double x) {
-    long long b = __double_as_longlong(x);
-    return b < 0 ? ~(uint64_t)b : ((uint64_t)b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(uint64_t k) {
-    long long b = (k & 0x8000000000000000ull) ? (long long)(k & 0x7fffffffffffffffull) : (long long)(~k);
-    return __longlong_as_double(b);
-}
 
 // k-th smallest (0-based) of the keys stored in scr[j*kScr + 6] (as bit patterns), j < n,
 // by an 8-pass radix select with a 256-bin shared-memory histogram per warp.
@@ -233,8 +225,9 @@ __global__ void k_src_geo(int32_t n_src, const double* __restrict__ src, double*
 }
 
 // Observation pass, one thread per observation (source order): residual h, design row A and
-// attitude partial g at the current parameters.  Scratch row: h, A[5], key(h/sigma), sigma^2.
-__global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, int64_t n_obs, const int64_t* __restrict__ t_ns,
+// attitude partial g at the current parameters.  Scratch row: h, A[5], key(h/sigma), sigma^2;
+// with the excess attitude noise on, sigma~^2 = sigma^2 + eps_a^2(t) in place of sigma^2 (Eq. W).
+__global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, AttNoise an, int64_t n_obs, const int64_t* __restrict__ t_ns,
                                                      const uint32_t* __restrict__ meta,
                                                      const float* __restrict__ sigma, const double* __restrict__ mu,
                                                      const int32_t* __restrict__ obs_src,
@@ -252,11 +245,16 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, int64_t n_obs, co
         ObsOut ob;
         observe<1>(G, S, t, m, muv, att, cal, ob);
         const double sg = (double)sigma[o];
+        double s2 = sg * sg, x = ob.R / sg;
+        if (an.eps2) {
+            s2 = s2 + an.eps2[an_index(an, t, m)];
+            x = ob.R / sqrt(s2);
+        }
         double* e = scr + (size_t)o * kScr;
         e[0] = ob.R;
         e[1] = ob.A[0]; e[2] = ob.A[1]; e[3] = ob.A[2]; e[4] = ob.A[3]; e[5] = ob.A[4];
-        e[6] = __longlong_as_double((long long)dkey(ob.R / sg));
-        e[7] = sg * sg;
+        e[6] = __longlong_as_double((long long)dkey(x));
+        e[7] = s2;
         ObsRec* r = rec + o;
         r->t_ns = t;
         r->meta = m;
@@ -569,7 +567,7 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
 }
 
 // the observation pass of the S block: source geometry, then the model at every observation
-void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+void launch_obs_pass(const DevGeo& G, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
                      const Shapes& sh, cudaStream_t stream) {
@@ -578,7 +576,7 @@ void launch_obs_pass(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta,
     int64_t fb = (n_obs + th - 1) / th;
     if (fb > 152 * (int64_t)sh.obs_bps) fb = 152 * (int64_t)sh.obs_bps;
     if (fb < 1) fb = 1;
-    k_obs_forward<<<(int)fb, th, 0, stream>>>(G, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
+    k_obs_forward<<<(int)fb, th, 0, stream>>>(G, an, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
 }
 
 // the per-source solves of the S block on the scratch rows of the observation pass

@@ -24,7 +24,7 @@ def test_library_builds_and_exports_all_declared_symbols():
     assert declared == set(agis.EXPORTS)
     for name in declared:
         assert hasattr(lib, name), name
-    assert lib.agis_abi_version() == agis.ABI_VERSION == 6
+    assert lib.agis_abi_version() == agis.ABI_VERSION == 7
 
 
 def test_default_config_and_struct_sizes():
