@@ -40,6 +40,8 @@ WORKLOADS = {
 # 4 rounds of sums, final pass, per-observation path, stats (two), history push = 15 (default
 # 4 reweighting rounds); A, C and frame as above.
 KERNELS_PER_STEP = {"fp64": (18, 18), "mixed": (2 + 15 + 12, 1 + 15 + 12)}
+# with the excess attitude noise on: x values, per-bucket selection, attitude weights
+KERNELS_ATTNOISE = 3
 FP64_PEAK_TFLOPS = 1.25
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per observation of the linearized observation pass (see time_form)
@@ -81,6 +83,9 @@ def parse():
     ap.add_argument("--orders", action="store_true",
                     help="with --convergence: also the Gauss-Seidel and Jacobi block orders (Sect. 4.6), mixed form")
     ap.add_argument("--asi-lambda-max", type=float, default=0.9, help="ASI: clamp of the lambda estimate")
+    ap.add_argument("--attnoise-s", type=float, default=0.0,
+                    help="estimate the excess attitude noise on buckets of this many seconds (FP64 form, "
+                         "--single-form; 0: off)")
     return ap.parse_args()
 
 
@@ -240,9 +245,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def time_form(agis, ds, stream, cfg, steps, warmup, local, dist, tune_iters=0):
+def time_form(agis, ds, stream, cfg, steps, warmup, local, dist, tune_iters=0, attnoise_ns=0):
     """Device-resident timing of `steps` iterations after `warmup` untimed ones; before the
-    warm-up, up to `tune_iters` iterations of the launch-shape autotuner (untimed)."""
+    warm-up, up to `tune_iters` iterations of the launch-shape autotuner (untimed).
+    attnoise_ns > 0: the excess attitude noise estimated on buckets of that length."""
     import torch
     # the context copies the observations into HBM at set-up; the timed iterations read only
     # device-resident data
@@ -251,6 +257,8 @@ def time_form(agis, ds, stream, cfg, steps, warmup, local, dist, tune_iters=0):
     g = agis.Agis(ds.geometry, cfg, obs_h, np.ascontiguousarray(ds.src0), np.ascontiguousarray(ds.att0),
                   np.ascontiguousarray(ds.cal0), src_ref=np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]),
                   stream=stream.cuda_stream)
+    if attnoise_ns > 0:
+        g.set_attnoise(attnoise_ns)
     t_init = time.perf_counter() - t
     del obs_h
     tuning = None
@@ -472,12 +480,16 @@ def main():
     forms = {"fp64": dict(precision=0), "mixed": dict(precision=1, refresh_every=args.refresh_every)}
     head = args.precision
     other = "mixed" if head == "fp64" else "fp64"
+    an_ns = int(round(args.attnoise_s * 1e9))
+    if an_ns > 0 and (head != "fp64" or not args.single_form):
+        raise SystemExit("--attnoise-s needs --precision fp64 --single-form")
     cfgs = {k: agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, **v) for k, v in forms.items()}
     # the mixed form is timed over whole refresh cycles, so its per-iteration time includes
     # the full FP64 evaluation at its share
     cyc = max(1, args.refresh_every)
     steps_of = {"fp64": args.steps, "mixed": cyc * max(1, -(-args.steps // cyc))}
-    res = {head: time_form(agis, ds, stream, cfgs[head], steps_of[head], args.warmup, local, dist, args.tune_iters)}
+    res = {head: time_form(agis, ds, stream, cfgs[head], steps_of[head], args.warmup, local, dist, args.tune_iters,
+                           an_ns)}
     if not args.single_form:
         res[other] = time_form(agis, ds, stream, cfgs[other], steps_of[other], args.warmup, local, dist,
                                args.tune_iters)
@@ -501,6 +513,8 @@ def main():
         ge = agis.Agis(ds.geometry, cfgs[head], host, src0, att0, cal0, src_ref=ref, stream=stream.cuda_stream)
         if r["tuning"]:
             ge.set_tuning(r["tuning"]["shapes"])
+        if an_ns > 0:
+            ge.set_attnoise(an_ns)
         ge.iterate(1)
         ge.sources(out=out_src.numpy())
         torch.cuda.synchronize()
@@ -554,11 +568,12 @@ def main():
                    "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "t_generate_s": round(t_gen, 1), "t_init_s": round(r["t_init"], 2),
-                   "autotune": r["tuning"]},
+                   "autotune": r["tuning"], "attnoise_bucket_s": args.attnoise_s or None},
         "e2e": ({"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
                 if e2e is not None else None),
         "gpu_launches": (KERNELS_PER_STEP[head][0] * r["n_full_eval"] +
-                         KERNELS_PER_STEP[head][1] * (steps_of[head] - r["n_full_eval"])),
+                         KERNELS_PER_STEP[head][1] * (steps_of[head] - r["n_full_eval"]) +
+                         (KERNELS_ATTNOISE * steps_of[head] if an_ns > 0 else 0)),
         "clocks": r["clocks"],
         "roofline": fp64_roofline(r) if head == "fp64" else mixed_roofline(r),
         "block_ms": summary(head, r)["block_ms"],
