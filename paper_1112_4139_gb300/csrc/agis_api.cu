@@ -65,9 +65,9 @@ void launch_int_sum(int n, const int* v, long long* out, cudaStream_t s);
 void launch_an_range(int64_t n, const int64_t* t, int64_t t0, unsigned long long* mx, int* neg, cudaStream_t s);
 void launch_an_keys(int64_t n, const int64_t* t, const uint32_t* meta, const AttNoise& an, int32_t* key, uint32_t* val,
                     cudaStream_t s);
-void launch_an_estimate(int64_t n, const AttNoise& an, double* eps2, const uint32_t* perm, const int64_t* off,
-                        const ObsRec* rec, const float* sigma, const int32_t* obs_src, const double* eps2_src,
-                        int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s);
+void launch_an_estimate(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
+                        const int64_t* off, const ObsRec* rec, const float* sigma, const int32_t* obs_src,
+                        const double* eps2_src, int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s);
 }  // namespace agis
 
 using namespace agis;
@@ -323,6 +323,7 @@ struct agis_ctx {
     // the (component, bucket) order and its run offsets, the x_l keys in that order, and the
     // attitude weights (source order)
     int64_t an_bucket_ns = 0;
+    int64_t an_max_run = 0;         // observations in the longest (component, bucket) run
     AttNoise an;
     double* an_eps2 = nullptr;
     uint32_t* an_perm = nullptr;
@@ -485,8 +486,8 @@ void enqueue_s_solve(agis_ctx* c) {
                             c->work, c->n_sblocks, c->sh, c->stream);
     // excess attitude noise from the residuals of this source update, and the attitude weights
     if (c->an.eps2)
-        launch_an_estimate(c->n_obs, c->an, c->an_eps2, c->an_perm, c->an_off, c->rec, c->sigma, c->obs_src,
-                           c->so.eps2, c->st.weight_fn, c->an_x, c->an_w, c->stream);
+        launch_an_estimate(c->n_obs, c->an, c->an_max_run, c->an_eps2, c->an_perm, c->an_off, c->rec, c->sigma,
+                           c->obs_src, c->so.eps2, c->st.weight_fn, c->an_x, c->an_w, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
                      c->sstat_part, c->stream);
     launch_hist_push(c->n_src, c->so.d, c->hist, c->stream);
@@ -1363,6 +1364,7 @@ int agis_set_attnoise(agis_ctx* c, int64_t bucket_ns) {
     c->an_w = nullptr;
     c->an = AttNoise{};
     c->an_bucket_ns = 0;
+    c->an_max_run = 0;
     if (bucket_ns == 0 || c->n_obs == 0) return AGIS_OK;
     const int64_t n = c->n_obs;
     cudaStream_t s = c->stream;
@@ -1403,7 +1405,11 @@ int agis_set_attnoise(agis_ctx* c, int64_t bucket_ns) {
         launch_an_keys(n, c->t_ns, c->meta, an, k_in, v_in, s);
         AGIS_TRY(sort_pairs(c, k_in, k_out, v_in, c->an_perm, n, bits_for(3 * n_b)));
         k_lower_bound<int32_t><<<grid_for(3 * n_b + 1, 256), 256, 0, s>>>(k_out, n, 3 * n_b + 1, c->an_off);
+        std::vector<int64_t> hoff(3 * (size_t)n_b + 1);
+        AGIS_CU(c, cudaMemcpyAsync(hoff.data(), c->an_off, hoff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                "set_attnoise (offsets)");
         AGIS_CU(c, cudaStreamSynchronize(s), "set_attnoise (order)");
+        for (size_t r = 0; r + 1 < hoff.size(); r++) c->an_max_run = std::max(c->an_max_run, hoff[r + 1] - hoff[r]);
     }
     an.eps2 = c->an_eps2;
     c->an = an;

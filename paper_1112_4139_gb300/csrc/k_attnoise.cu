@@ -12,16 +12,19 @@
 // sigma~_l^2 = sigma_l^2 + eps_a^2(t_l) (in the observation pass).
 //
 // Layout: a permutation of the observations sorted once by (component, bucket) makes every
-// bucket a contiguous run; x_l is written in that order as an order-preserving 64-bit key,
-// and one block per run selects the two order statistics around 0.68 (n - 1) exactly by a
-// radix select (8 passes of 8 bits, counts in shared memory), so the estimate does not
-// depend on timing or launch shape.  Runs up to kSelCache keys are staged in shared memory.
+// bucket a contiguous run; x_l is written in that order as an order-preserving 64-bit key.
+// The two order statistics around 0.68 (n - 1) of a run are selected exactly by a radix
+// select (passes of 8 bits, counts in shared memory), so the estimate does not depend on
+// timing or launch shape: one warp per run of up to kWarpRun keys (no block barriers; a pass
+// whose chosen digit holds a single key ends the select, about 4 passes instead of 8 on
+// continuous data), one block per longer run.
 #include "agis_internal.cuh"
 
 namespace agis {
 
 constexpr int kSelThreads = 256;
-constexpr int kSelCache = 4096;   // 32 KB of keys
+constexpr int kSelWarps = 8;      // warps per block of the warp-per-run kernel
+constexpr int kWarpRun = 4096;    // longest run of the warp-per-run kernel
 
 // largest t - t0 over the observations, and a flag for any t < t0
 __global__ void k_an_range(int64_t n, const int64_t* __restrict__ t, int64_t t0, unsigned long long* __restrict__ mx,
@@ -70,11 +73,20 @@ __global__ void k_an_values(int64_t n, const uint32_t* __restrict__ perm, const 
     }
 }
 
-// eps_a^2 of each (component, bucket) run: one block per run (grid-stride over runs)
+// linear interpolation between the order statistics a = x_(k) and b = x_(k+1) at weight
+// gamma, from the nearer end, each operation rounded on its own; clamped at 0 (Eq. e09)
+__device__ __forceinline__ double quantile_clamped(uint64_t ka, uint64_t kb, double gamma) {
+    const double a = dkey_inv(ka), b = dkey_inv(kb);
+    const double diff = __dadd_rn(b, -a);
+    const double val = gamma >= 0.5 ? __dadd_rn(b, -__dmul_rn(diff, __dadd_rn(1.0, -gamma)))
+                                    : __dadd_rn(a, __dmul_rn(diff, gamma));
+    return val > 0.0 ? val : 0.0;
+}
+
+// eps_a^2 of the runs longer than kWarpRun: one block per run (grid-stride over runs)
 __global__ void __launch_bounds__(kSelThreads) k_an_select(int n_run, const int64_t* __restrict__ off,
                                                            const uint64_t* __restrict__ xkey, double q,
                                                            double* __restrict__ eps2) {
-    __shared__ uint64_t cache[kSelCache];
     __shared__ unsigned long long hist[256];
     __shared__ int sh_bin;
     __shared__ long long sh_below;
@@ -83,15 +95,8 @@ __global__ void __launch_bounds__(kSelThreads) k_an_select(int n_run, const int6
     for (int run = blockIdx.x; run < n_run; run += gridDim.x) {
         const int64_t lo = off[run];
         const int64_t n = off[run + 1] - lo;
-        if (n == 0) {
-            if (threadIdx.x == 0) eps2[run] = 0.0;
-            continue;
-        }
+        if (n <= kWarpRun) continue;   // the warp-per-run kernel's (the same for the whole block)
         const uint64_t* v = xkey + lo;
-        if (n <= kSelCache) {
-            for (int64_t j = threadIdx.x; j < n; j += blockDim.x) cache[j] = v[j];
-            v = cache;
-        }
         // virtual index h = q (n - 1): order statistics k = floor(h) and k + 1, weight h - k
         const double h = q * (double)(n - 1);
         const double fl = floor(h);
@@ -165,15 +170,112 @@ __global__ void __launch_bounds__(kSelThreads) k_an_select(int n_run, const int6
         __syncthreads();
         if (threadIdx.x == 0) {
             const uint64_t k1 = (k + 1 < n && sh_cle <= (unsigned long long)(k + 1)) ? sh_nxt : prefix;
-            const double a = dkey_inv(prefix), b = dkey_inv(k1);
-            const double gamma = h - fl;
-            const double diff = __dadd_rn(b, -a);
-            // linear interpolation, from the nearer end
-            const double val = gamma >= 0.5 ? __dadd_rn(b, -__dmul_rn(diff, __dadd_rn(1.0, -gamma)))
-                                            : __dadd_rn(a, __dmul_rn(diff, gamma));
-            eps2[run] = val > 0.0 ? val : 0.0;
+            eps2[run] = quantile_clamped(prefix, k1, h - fl);
         }
         __syncthreads();
+    }
+}
+
+// eps_a^2 of the runs of up to kWarpRun keys (empty runs included): one warp per run
+__global__ void __launch_bounds__(32 * kSelWarps) k_an_select_warp(int n_run, const int64_t* __restrict__ off,
+                                                                   const uint64_t* __restrict__ xkey, double q,
+                                                                   double* __restrict__ eps2) {
+    __shared__ unsigned int hist_all[kSelWarps][256];
+    const int lane = threadIdx.x & 31;
+    unsigned int* hist = hist_all[threadIdx.x >> 5];
+    const int n_warps = gridDim.x * kSelWarps;
+    for (int run = blockIdx.x * kSelWarps + (threadIdx.x >> 5); run < n_run; run += n_warps) {
+        const int64_t lo = off[run];
+        const int64_t n64 = off[run + 1] - lo;
+        if (n64 > kWarpRun) continue;   // the block kernel's
+        const int n = (int)n64;
+        if (n == 0) {
+            if (lane == 0) eps2[run] = 0.0;
+            continue;
+        }
+        const uint64_t* v = xkey + lo;
+        const double h = q * (double)(n - 1);
+        const double fl = floor(h);
+        const int k = (int)fl;
+        uint64_t prefix = 0;
+        int kk = k;
+        for (int d = 7; d >= 0; d--) {
+            const int shift = 8 * d;
+            const uint64_t hmask = d == 7 ? 0ull : (~0ull << (shift + 8));
+            for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+            __syncwarp();
+            for (int j = lane; j < n; j += 32) {
+                const uint64_t key = v[j];
+                if (((key ^ prefix) & hmask) == 0ull) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+            }
+            __syncwarp();
+            unsigned int c[8], sum = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                c[i] = hist[lane * 8 + i];
+                sum += c[i];
+            }
+            unsigned int incl = sum;
+            for (int s = 1; s < 32; s <<= 1) {
+                const unsigned int up = __shfl_up_sync(0xffffffffu, incl, s);
+                if (lane >= s) incl += up;
+            }
+            const unsigned int excl = incl - sum;
+            const bool holds = (unsigned int)kk >= excl && (unsigned int)kk < incl;
+            int bin = 0, below = 0, cnt = 0;
+            if (holds) {
+                unsigned int bl = excl;
+                for (int i = 0; i < 8; i++) {
+                    if ((unsigned int)kk < bl + c[i]) {
+                        bin = lane * 8 + i;
+                        below = (int)bl;
+                        cnt = (int)c[i];
+                        break;
+                    }
+                    bl += c[i];
+                }
+            }
+            const int src = __ffs(__ballot_sync(0xffffffffu, holds)) - 1;
+            bin = __shfl_sync(0xffffffffu, bin, src);
+            below = __shfl_sync(0xffffffffu, below, src);
+            cnt = __shfl_sync(0xffffffffu, cnt, src);
+            prefix |= (uint64_t)bin << shift;
+            kk -= below;
+            __syncwarp();   // the histogram is read before the next pass clears it
+            if (cnt == 1 && d > 0) {
+                // one key carries this prefix down to digit d: it is the k-th
+                uint64_t cand = ~0ull;
+                for (int j = lane; j < n; j += 32) {
+                    const uint64_t key = v[j];
+                    if (((key ^ prefix) >> shift) == 0ull && key < cand) cand = key;
+                }
+                for (int s = 16; s > 0; s >>= 1) {
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, cand, s);
+                    cand = o < cand ? o : cand;
+                }
+                prefix = cand;
+                break;
+            }
+        }
+        // the next order statistic, as in the block kernel
+        unsigned int cle = 0;
+        uint64_t nxt = ~0ull;
+        for (int j = lane; j < n; j += 32) {
+            const uint64_t key = v[j];
+            if (key <= prefix)
+                cle++;
+            else if (key < nxt)
+                nxt = key;
+        }
+        for (int s = 16; s > 0; s >>= 1) {
+            cle += __shfl_xor_sync(0xffffffffu, cle, s);
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, nxt, s);
+            nxt = o < nxt ? o : nxt;
+        }
+        if (lane == 0) {
+            const uint64_t k1 = (k + 1 < n && cle <= (unsigned int)(k + 1)) ? nxt : prefix;
+            eps2[run] = quantile_clamped(prefix, k1, h - fl);
+        }
     }
 }
 
@@ -207,15 +309,20 @@ void launch_an_keys(int64_t n, const int64_t* t, const uint32_t* meta, const Att
 }
 
 // eps_a^2 from the residuals of the source update just made, then the attitude weights.
-// an.eps2 and eps2 are the same array (written here).
-void launch_an_estimate(int64_t n, const AttNoise& an, double* eps2, const uint32_t* perm, const int64_t* off,
-                        const ObsRec* rec, const float* sigma, const int32_t* obs_src, const double* eps2_src,
-                        int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s) {
+// an.eps2 and eps2 are the same array (written here); max_run: the longest run (the block
+// kernel runs only when some run is longer than kWarpRun).
+void launch_an_estimate(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
+                        const int64_t* off, const ObsRec* rec, const float* sigma, const int32_t* obs_src,
+                        const double* eps2_src, int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s) {
     if (n == 0 || an.n_b == 0) return;
     k_an_values<<<an_grid(n), 256, 0, s>>>(n, perm, rec, sigma, obs_src, eps2_src, xkey);
     const int n_run = 3 * an.n_b;
-    const int blocks = n_run < 152 * 8 ? n_run : 152 * 8;
-    k_an_select<<<blocks, kSelThreads, 0, s>>>(n_run, off, xkey, 0.68, eps2);
+    const int wblocks = (n_run + kSelWarps - 1) / kSelWarps;
+    k_an_select_warp<<<wblocks < 152 * 16 ? wblocks : 152 * 16, 32 * kSelWarps, 0, s>>>(n_run, off, xkey, 0.68, eps2);
+    if (max_run > kWarpRun) {
+        const int blocks = n_run < 152 * 8 ? n_run : 152 * 8;
+        k_an_select<<<blocks, kSelThreads, 0, s>>>(n_run, off, xkey, 0.68, eps2);
+    }
     k_an_weights<<<an_grid(n), 256, 0, s>>>(n, an, rec, sigma, obs_src, eps2_src, weight_fn, w_att);
 }
 
