@@ -48,8 +48,10 @@ FALLBACK_HBM_GBS = 6800.0
 MIX_PASS_BYTES = 8 + 16 + 4 + 8 + 8
 # DRAM bytes per observation (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
 # of 2.47e7 observations, scaled per observation; profiles/k_*_kernels_30k.md): the S block of
-# the FP64 form (observation pass + solves) and the mixed form's linearized pass
-TRAFFIC_PER_OBS = {"fp64_s_block": 862.2, "mixed_correct": 47.6}
+# the FP64 form (observation pass + solves) and the mixed form's linearized pass.  None once
+# the kernel has changed since its capture: the FP64 observation pass took the attitude-noise
+# descriptor after its capture (862 B/obs before).
+TRAFFIC_PER_OBS = {"fp64_s_block": None, "mixed_correct": 47.6}
 
 
 def parse():
@@ -531,7 +533,8 @@ def main():
         achieved = S_FLOPS_PER_OBS * ds.n_obs / (x["s_ms"] * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_obs_forward + k_source_solve (S block, FP64)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_PER_OBS["fp64_s_block"] * ds.n_obs,
+                "traffic": (TRAFFIC_PER_OBS["fp64_s_block"] * ds.n_obs
+                            if TRAFFIC_PER_OBS["fp64_s_block"] is not None else None),
                 "peak_source": "FP64 nominal 1.25 TFLOP/s (unit count x clock)", "flops_per_obs": S_FLOPS_PER_OBS}
 
     def mixed_roofline(x):
