@@ -19,6 +19,9 @@ Modules and the passages they follow:
   agis      Sect. 4.6 (the S[ACG] simple iteration)
   asi       Sect. 4.7 (the accelerated simple iteration)
   attnoise  Sect. 5.2.5 (the excess attitude noise, Eqs. excess, W, wl, e09)
+  calgeneric Sects. 3.4 and 5.3 (the full geometric calibration: observation-line terms of
+            Eq. etazeta, the block-diagonal update of Eqs. normC and calCon with the
+            constraints of Eqs. cc1-cc3, the basic angle of Eq. DeltaGamma)
   mlp       the learned iteration proposal (not in the paper; analogue of the
             accelerated simple iteration of Sect. 4.7): network, loss, gradient,
             Adam, features and targets
