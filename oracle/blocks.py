@@ -32,6 +32,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import calgeneric as CG
 from . import cholesky as CH
 from . import model as M
 from . import quat as Q
@@ -273,7 +274,11 @@ def calibration_update(P, cal, ev, R, W):
     N = 0) and the constraint projection d = d~ - C (C'C)^-1 C' d~ (Eq. calCon).  The
     constraint columns of Eqs. cc1 and cc3 have disjoint supports, so C'C is diagonal and
     the projection subtracts, within each column's support, C'd~ / C'C.
+    With the full calibration model (P.calg) the update of oracle/calgeneric.py instead.
     Returns (new calibration, rank defect)."""
+    if P.calg is not None:
+        d, rd = CG.update(P.calg, ev["cal_cols"], ev["cal_vals"], R, W)
+        return np.asarray(cal) + d, rd
     k = ev["cal_k"]
     Ncc = np.bincount(k, weights=W, minlength=P.n_cal)
     bc = np.bincount(k, weights=-R * W, minlength=P.n_cal)

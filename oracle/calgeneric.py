@@ -182,29 +182,27 @@ def cc2_weights(L):
 
 def group_normals(L, cols, vals, R, W):
     """Dense normals N, b = -sum Phi R W (Eq. normC) of every AL group [n_groups, s, s] and AC
-    group [n_groups, 6, 6], s = al_size."""
+    group [n_groups, 6, 6], s = al_size: the sums over observations of W Phi Phi' and
+    -W Phi R, scattered into the group of each observation."""
     s = L.al_size
-    Nal = np.zeros((L.n_groups, s, s))
-    bal = np.zeros((L.n_groups, s))
-    Nac = np.zeros((L.n_groups, 6, 6))
-    bac = np.zeros((L.n_groups, 6))
     R = np.asarray(R, dtype=np.float64)
     W = np.asarray(W, dtype=np.float64)
-    for l in range(cols.shape[0]):
-        c = cols[l]
-        used = c >= 0
-        c, v = c[used], vals[l][used]
-        if c[0] < L.n_al:
-            gi, loc = np.divmod(c, s)
-            g = gi[0]
-            Nal[g][np.ix_(loc, loc)] += np.outer(v, v) * W[l]
-            bal[g][loc] -= v * R[l] * W[l]
-        else:
-            gi, loc = np.divmod(c - L.n_al, 6)
-            g = gi[0]
-            Nac[g][np.ix_(loc, loc)] += np.outer(v, v) * W[l]
-            bac[g][loc] -= v * R[l] * W[l]
-    return Nal, bal, Nac, bac
+    al = cols[:, 0] < L.n_al
+    out = []
+    for sel, base, size, nslot in ((al, 0, s, 4), (~al, L.n_al, 6, 3)):
+        c = cols[sel][:, :nslot] - base
+        v = vals[sel][:, :nslot]
+        g = c[:, 0] // size
+        loc = c - g[:, None] * size
+        N = np.zeros(L.n_groups * size * size)
+        b = np.zeros(L.n_groups * size)
+        w, r = W[sel], R[sel]
+        for a in range(nslot):
+            for e in range(nslot):
+                np.add.at(N, (g * size + loc[:, a]) * size + loc[:, e], w * v[:, a] * v[:, e])
+            np.add.at(b, g * size + loc[:, a], -v[:, a] * r * w)
+        out += [N.reshape(L.n_groups, size, size), b.reshape(L.n_groups, size)]
+    return out[0], out[1], out[2], out[3]
 
 
 def cc2_matrix(L):

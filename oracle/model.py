@@ -21,6 +21,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import calgeneric as CG
 from . import quat as Q
 from . import spline
 
@@ -62,6 +63,10 @@ class Problem:
     sigma: np.ndarray
     mu: np.ndarray
     n_src: int
+    # full geometric calibration (Eq. etazeta): its layout and the gate of each observation;
+    # None: the per-day offsets
+    calg: object = None
+    gate: np.ndarray = None
 
     @property
     def n_obs(self):
@@ -69,6 +74,8 @@ class Problem:
 
     @property
     def n_cal(self):
+        if self.calg is not None:
+            return int(self.calg.n_params)
         return int(self.n_cal_days * 2 * (62 + 7))
 
     def knots(self):
@@ -91,7 +98,10 @@ def problem_from_dataset(ds):
         knot0_ns=int(g["knot0_ns"]), knot_dt_ns=int(g["knot_dt_ns"]), n_coef=int(g["n_coef"]),
         cal_t0_ns=int(g["cal_t0_ns"]), cal_dt_ns=int(g["cal_dt_ns"]), n_cal_days=int(g["n_cal_days"]),
         t_ns=ds.t_ns, src=ds.src, ccd=ds.ccd, fov=ds.fov, kind=ds.kind, sigma=ds.sigma, mu=ds.mu,
-        n_src=ds.n_src)
+        n_src=ds.n_src,
+        calg=(CG.Layout(n_ccd=62, n_gate=int(g["n_gate"]), n_j=int(g["n_cal_days"]), j_per_k=int(g["cal_j_per_k"]),
+                        n_col=int(g["n_col"]), col_bin=int(g["cal_col_bin"])) if g.get("cal_generic") else None),
+        gate=ds.gate)
 
 
 # ---------------------------------------------------------------------------
@@ -189,13 +199,20 @@ def field_angles(u_srs):
 
 def observation_lines(P, cal, idx=slice(None)):
     """Calibrated observation lines eta_fng and zeta_fng of the observations, Eqs. etazeta0 and
-    etazeta (r = 0 offsets)."""
+    etazeta: the r = 0 offsets, or with P.calg the full model (oracle/calgeneric.py; the nominal
+    lines the same for every gate).  Returns (lines, k): k the parameter index of each
+    observation, or with P.calg the (cols, vals) of its calibration terms."""
     t_ns, fov, ccd, kind, mu = P.t_ns[idx], P.fov[idx], P.ccd[idx], P.kind[idx], P.mu[idx]
-    k = cal_index(P, t_ns, fov, ccd, kind)
-    eta_line = P.eta0[ccd] + cal[k]
+    if P.calg is not None:
+        k = CG.design(P.calg, kind, fov, ccd, P.gate[idx], cal_day(P, t_ns), mu)
+        term = CG.line_term(cal, *k)
+    else:
+        k = cal_index(P, t_ns, fov, ccd, kind)
+        term = np.asarray(cal)[k]
+    eta_line = P.eta0[ccd] + term
     f = np.where(fov == 0, 0, 1)
     zeta0 = -(P.x_fpa[ccd] - (mu - P.mu_c) * P.p_ac - P.x_centre[f]) / P.focal_length
-    zeta_line = zeta0 + cal[k]
+    zeta_line = zeta0 + term
     return np.where(kind == 0, eta_line, zeta_line), k
 
 
@@ -208,7 +225,8 @@ def evaluate(P, src, att, cal, idx=slice(None), knots=None, partials=True):
       A      design rows -dR/ds' (5 per observation), Eqs. dfads, srsprop1diffsol, ubardiff, duds
       gq     dR/dq (4 per observation, quaternion), Eq. dfadq
       s      unnormalised spline sum (4), B (4 B-splines), l (left index)
-      cal_k  calibration parameter index (dR/dc_k = +1, Eq. pdC)
+      cal_k  calibration parameter index (dR/dc_k = +1, Eq. pdC); with the full calibration
+             model cal_cols, cal_vals instead (dR/dc = the factor, Eq. pdC)
     """
     t_ns = P.t_ns[idx]
     s5 = np.asarray(src)[P.src[idx]]
@@ -221,7 +239,11 @@ def evaluate(P, src, att, cal, idx=slice(None), knots=None, partials=True):
     eta = phi - f * P.gamma_c / 2.0                                   # Eq. srspropeta
     line, k = observation_lines(P, cal, idx)
     R = np.where(kind == 0, line - eta, line - zeta)
-    out = dict(R=R, s=s, B=B, l=l, cal_k=k, phi=phi, zeta=zeta, u=u, q=qa)
+    out = dict(R=R, s=s, B=B, l=l, phi=phi, zeta=zeta, u=u, q=qa)
+    if P.calg is not None:
+        out.update(cal_k=None, cal_cols=k[0], cal_vals=k[1])
+    else:
+        out.update(cal_k=k)
     if not partials:
         return out
     # source partials

@@ -26,6 +26,12 @@ Recipe (readings of the paper where it is silent):
     (field, row, day) AC offsets N(0, 5 mas), projected onto the constraints
     (zero mean over the 124 AL offsets of a day, over the 7 AC offsets of a
     field and day).
+  * full geometric calibration (cal_generic): the terms of Eq. etazeta per CCD and gate in the
+    layout of oracle/calgeneric.py (r = 0 AL terms N(0, 0.5 mas), r = 1, 2 terms N(0, 0.1 mas),
+    small-scale AL terms N(0, 0.05 mas), r = 0 AC terms N(0, 5 mas) on the AF1 CCDs, made to
+    satisfy Eqs. cc1-cc3); an observation of a source of magnitude G is gated when G plus a
+    N(0, 0.15 mag) jitter is below 13 (gate 1 + floor((13 - G') / 0.5)); AL observations record
+    the AC pixel coordinate of the image (mu from the nominal AC line at the true zeta).
   * observables: the crossing time of the calibrated observation line is solved
     on the true model, so that the residual at truth equals the injected noise
     (Gaussian, plus 1% of components offset by +-10 sigma); times are rounded
@@ -70,6 +76,9 @@ class _SimConfig(C.Structure):
         ("start_att_err", C.c_double), ("min_transits", C.c_int32), ("max_transits", C.c_int32),
         ("dec_min", C.c_double), ("dec_max", C.c_double), ("ra_min", C.c_double), ("ra_max", C.c_double),
         ("parallax_mean", C.c_double), ("pm_sigma", C.c_double), ("n_threads", C.c_int32),
+        ("cal_generic", C.c_int32), ("n_gate", C.c_int32), ("cal_j_per_k", C.c_int32), ("cal_col_bin", C.c_int32),
+        ("gate_g0", C.c_double), ("gate_step", C.c_double), ("gate_fuzz", C.c_double),
+        ("cal_l12_rms", C.c_double), ("cal_small_rms", C.c_double),
     ]
 
 
@@ -119,6 +128,7 @@ def _load():
         P = C.c_void_p
         lib.sim_copy_obs.argtypes = [C.c_void_p] + [P] * 8
         lib.sim_copy_truth.argtypes = [C.c_void_p] + [P] * 5
+        lib.sim_copy_gate.argtypes = [C.c_void_p, P]
         lib.sim_starting_values.argtypes = [C.c_void_p] + [P] * 3
         lib.sim_field_angles.argtypes = [C.c_void_p, P, C.c_int64, P, P]
         lib.sim_target_quat.argtypes = [C.c_void_p, C.c_double, P]
@@ -158,6 +168,16 @@ class SimConfig:
     parallax_mean: float = 1 * MAS
     pm_sigma: float = 10 * MAS
     n_threads: int = 0
+    # the full geometric calibration of Eq. etazeta instead of per-day offsets
+    cal_generic: bool = False
+    n_gate: int = 1
+    cal_j_per_k: int = 1
+    cal_col_bin: int = 1
+    gate_g0: float = 13.0
+    gate_step: float = 0.5
+    gate_fuzz: float = 0.15
+    cal_l12_rms: float = 0.1 * MAS
+    cal_small_rms: float = 0.05 * MAS
 
     def span_ns(self) -> int:
         # whole number of knot intervals
@@ -188,6 +208,7 @@ class Dataset:
     src0: np.ndarray
     att0: np.ndarray
     cal0: np.ndarray
+    gate: np.ndarray = None   # per observation (0: not gated); all 0 unless cfg.cal_generic
 
     @property
     def n_obs(self) -> int:
@@ -222,7 +243,8 @@ class Dataset:
         return dataclasses.replace(
             self, t_ns=sel(self.t_ns), src=sel(remap[self.src]).astype(np.int32), ccd=sel(self.ccd),
             fov=sel(self.fov), kind=sel(self.kind), sigma=sel(self.sigma), mu=sel(self.mu),
-            noise=sel(self.noise), src_true=self.src_true[idx].copy(), src_mag=self.src_mag[idx].copy(),
+            noise=sel(self.noise), gate=sel(self.gate), src_true=self.src_true[idx].copy(),
+            src_mag=self.src_mag[idx].copy(),
             n_transits=self.n_transits[idx].copy(), src0=self.src0[idx].copy())
 
 
@@ -246,6 +268,10 @@ def simulate(cfg: SimConfig) -> Dataset:
     c.ra_min, c.ra_max = cfg.ra_range
     c.parallax_mean, c.pm_sigma = cfg.parallax_mean, cfg.pm_sigma
     c.n_threads = cfg.n_threads
+    c.cal_generic = int(cfg.cal_generic)
+    c.n_gate, c.cal_j_per_k, c.cal_col_bin = cfg.n_gate, cfg.cal_j_per_k, cfg.cal_col_bin
+    c.gate_g0, c.gate_step, c.gate_fuzz = cfg.gate_g0, cfg.gate_step, cfg.gate_fuzz
+    c.cal_l12_rms, c.cal_small_rms = cfg.cal_l12_rms, cfg.cal_small_rms
     h = lib.sim_create(C.byref(c))
     try:
         n_obs = lib.sim_generate(h)
@@ -264,6 +290,8 @@ def simulate(cfg: SimConfig) -> Dataset:
         noise = np.empty(n_obs, np.float64)
         ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
         lib.sim_copy_obs(h, ptr(t_ns), ptr(src), ptr(ccd), ptr(fov), ptr(kind), ptr(sigma), ptr(mu), ptr(noise))
+        gate = np.empty(n_obs, np.uint8)
+        lib.sim_copy_gate(h, ptr(gate))
         src_true = np.empty((n_src, 5))
         src_mag = np.empty(n_src)
         n_tr = np.empty(n_src, np.int32)
@@ -285,9 +313,12 @@ def simulate(cfg: SimConfig) -> Dataset:
         n_coef=g.n_coef, cal_t0_ns=0, cal_dt_ns=c.cal_dt_ns, n_cal_days=g.n_cal_days,
         span_ns=c.span_ns, spin_rate=g.spin_rate,
     )
+    if cfg.cal_generic:
+        geometry.update(cal_generic=1, n_gate=cfg.n_gate, cal_j_per_k=cfg.cal_j_per_k, cal_col_bin=cfg.cal_col_bin,
+                        n_col=1966)
     return Dataset(cfg=cfg, geometry=geometry, t_ns=t_ns, src=src, ccd=ccd, fov=fov, kind=kind, sigma=sigma,
                    mu=mu, noise=noise, src_true=src_true, src_mag=src_mag, n_transits=n_tr, att_true=att_true,
-                   cal_true=cal_true, src0=src0, att0=att0, cal0=cal0)
+                   cal_true=cal_true, src0=src0, att0=att0, cal0=cal0, gate=gate)
 
 
 def config(name: str, **over) -> SimConfig:

@@ -68,6 +68,17 @@ typedef struct {
     double parallax_mean;     /* rad */
     double pm_sigma;          /* rad/yr */
     int32_t n_threads;        /* 0: default */
+    /* full geometric calibration of Eq. etazeta (cal_generic = 1); otherwise the per-day
+     * offsets above */
+    int32_t cal_generic;
+    int32_t n_gate;           /* gates 0 .. n_gate - 1 */
+    int32_t cal_j_per_k;      /* days (short intervals) per long interval */
+    int32_t cal_col_bin;      /* pixel columns per small-scale parameter */
+    double gate_g0;           /* observations of sources brighter than this magnitude are gated */
+    double gate_step;         /* magnitudes per gate */
+    double gate_fuzz;         /* rms of the per-observation jitter of the gate threshold (mag) */
+    double cal_l12_rms;       /* rad, the r = 1, 2 large-scale AL and AC terms */
+    double cal_small_rms;     /* rad, the small-scale AL terms */
 } sim_config;
 
 typedef struct {
@@ -489,10 +500,11 @@ typedef struct {
     float *sigma;
     double *mu;
     double *noise; /* realised R at truth (for tests) */
+    uint8_t *gate;
 } obs_buf;
 
 static void buf_push(obs_buf *b, int64_t t, int32_t src, int ccd, int fov, int kind, float sig, double mu,
-                     double noise) {
+                     double noise, int gate) {
     if (b->n == b->cap) {
         int64_t nc = b->cap ? 2 * b->cap : 4096;
         b->t_ns = realloc(b->t_ns, nc * sizeof(int64_t));
@@ -503,11 +515,12 @@ static void buf_push(obs_buf *b, int64_t t, int32_t src, int ccd, int fov, int k
         b->sigma = realloc(b->sigma, nc * sizeof(float));
         b->mu = realloc(b->mu, nc * sizeof(double));
         b->noise = realloc(b->noise, nc * sizeof(double));
+        b->gate = realloc(b->gate, nc);
         b->cap = nc;
     }
     int64_t i = b->n++;
     b->t_ns[i] = t; b->src[i] = src; b->ccd[i] = (uint8_t)ccd; b->fov[i] = (uint8_t)fov;
-    b->kind[i] = (uint8_t)kind; b->sigma[i] = sig; b->mu[i] = mu; b->noise[i] = noise;
+    b->kind[i] = (uint8_t)kind; b->sigma[i] = sig; b->mu[i] = mu; b->noise[i] = noise; b->gate[i] = (uint8_t)gate;
 }
 
 typedef struct sim_handle {
@@ -538,6 +551,77 @@ static inline int64_t cal_index_ac(const sim_geometry *g, int64_t day, int fov, 
     return g->n_cal_days * 2 * SIM_NCCD + (day * 2 + fov) * SIM_NROW + row;
 }
 
+/* full geometric calibration, parameter layout: groups (ccd, gate, long interval k) in that
+ * order; within an AL group Deta[j in k][f][r] (6 per day) then deta[bin]; all AC groups after
+ * all AL groups, Dzeta[f][r] (6 each) */
+#define SIM_NCOL 1966
+typedef struct {
+    int64_t n_j, j_per_k, n_k, n_gate, col_bin, n_bin, al_size, n_groups, n_al;
+} gen_layout;
+static gen_layout gen_layout_of(const sim_config *c, const sim_geometry *g) {
+    gen_layout L;
+    L.n_j = g->n_cal_days;
+    L.j_per_k = c->cal_j_per_k > 0 ? c->cal_j_per_k : 1;
+    L.n_k = (L.n_j + L.j_per_k - 1) / L.j_per_k;
+    L.n_gate = c->n_gate > 0 ? c->n_gate : 1;
+    L.col_bin = c->cal_col_bin > 0 ? c->cal_col_bin : 1;
+    L.n_bin = (SIM_NCOL + L.col_bin - 1) / L.col_bin;
+    L.al_size = 6 * L.j_per_k + L.n_bin;
+    L.n_groups = (int64_t)SIM_NCCD * L.n_gate * L.n_k;
+    L.n_al = L.n_groups * L.al_size;
+    return L;
+}
+static inline int64_t gen_group(const gen_layout *L, int ccd, int gate, int64_t k) {
+    return ((int64_t)ccd * L->n_gate + gate) * L->n_k + k;
+}
+static inline int64_t gen_deta(const gen_layout *L, int ccd, int gate, int64_t j, int fov, int r) {
+    return gen_group(L, ccd, gate, j / L->j_per_k) * L->al_size + (j % L->j_per_k) * 6 + fov * 3 + r;
+}
+static inline int64_t gen_small(const gen_layout *L, int ccd, int gate, int64_t k, int64_t b) {
+    return gen_group(L, ccd, gate, k) * L->al_size + 6 * L->j_per_k + b;
+}
+static inline int64_t gen_dzeta(const gen_layout *L, int ccd, int gate, int64_t k, int fov, int r) {
+    return L->n_al + gen_group(L, ccd, gate, k) * 6 + fov * 3 + r;
+}
+/* shifted Legendre polynomials L*_0..2 at x = (mu - 13.5) / 1966 */
+static inline void gen_legendre(double mu, double l[3]) {
+    double x = (mu - 13.5) / SIM_NCOL;
+    l[0] = 1.0;
+    l[1] = 2.0 * x - 1.0;
+    l[2] = 6.0 * x * x - 6.0 * x + 1.0;
+}
+static inline int64_t gen_bin(const gen_layout *L, double mu) {
+    int64_t m = (int64_t)floor(mu + 0.5) - 14;
+    if (m < 0) m = 0;
+    if (m > SIM_NCOL - 1) m = SIM_NCOL - 1;
+    return m / L->col_bin;
+}
+/* the calibration terms of an AL and of an AC observation line (Eq. etazeta) */
+static double gen_al_term(const gen_layout *L, const double *cal, int ccd, int gate, int64_t day, int fov,
+                          double mu) {
+    double l[3];
+    gen_legendre(mu, l);
+    double v = 0.0;
+    for (int r = 0; r < 3; r++) v += cal[gen_deta(L, ccd, gate, day, fov, r)] * l[r];
+    return v + cal[gen_small(L, ccd, gate, day / L->j_per_k, gen_bin(L, mu))];
+}
+static double gen_ac_term(const gen_layout *L, const double *cal, int ccd, int gate, int64_t day, int fov,
+                          double mu) {
+    double l[3];
+    gen_legendre(mu, l);
+    double v = 0.0;
+    for (int r = 0; r < 3; r++) v += cal[gen_dzeta(L, ccd, gate, day / L->j_per_k, fov, r)] * l[r];
+    return v;
+}
+/* gate of one observation: the source magnitude with a jittered threshold */
+static int gen_gate(const sim_config *c, double G, rng_t *rg) {
+    if (!c->cal_generic || c->n_gate <= 1) return 0;
+    double Gj = G + c->gate_fuzz * rng_gauss(rg);
+    if (Gj >= c->gate_g0) return 0;
+    int g = 1 + (int)floor((c->gate_g0 - Gj) / c->gate_step);
+    return g > c->n_gate - 1 ? c->n_gate - 1 : g;
+}
+
 static int64_t day_of(const sim_config *c, const sim_geometry *g, int64_t t_ns) {
     int64_t d = t_ns / c->cal_dt_ns;
     if (d < 0) d = 0;
@@ -559,6 +643,11 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
     }
     rng_t rn;
     rng_seed(&rn, c->seed, 0x5EEDULL + 7, (uint64_t)i);
+    /* gates draw from their own stream: the offsets-only data stay as they were */
+    rng_t rg;
+    rng_seed(&rg, c->seed, 0x6A7EULL, (uint64_t)i);
+    const gen_layout GL = gen_layout_of(c, g);
+    const int generic = c->cal_generic != 0;
     const double T = 2.0 * SIM_PI / g->spin_rate;
     const double span_s = (double)c->span_ns * 1e-9;
     const int64_t n_rev = h->n_rev;
@@ -625,13 +714,19 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
                         eps += (rng_uniform(&rn) < 0.5 ? -1.0 : 1.0) * c->outlier_nsigma * sig_al;
                 }
                 double eta0 = g->eta0[ccd];
+                const int gate = gen_gate(c, h->src_mag[i], &rg);
                 double o = have_last ? o_last + (eta0 - eta0_last) / slope : o_start;
                 int64_t day = day_of(c, g, base + (int64_t)llround(o));
-                double target = eta0 + h->cal_true[cal_index_al(g, day, fi, ccd)] - eps;
+                double target = generic ? 0.0 : eta0 + h->cal_true[cal_index_al(g, day, fi, ccd)] - eps;
                 double o_prev = 0, e_prev = 0, e = 0;
                 int converged = 0;
                 for (int it = 0; it < 12; it++) {
                     field_angles(g, dt, coef, &sg, base, o, &ph, &ze);
+                    if (generic) {
+                        /* the line at the AC pixel coordinate of the image at this time */
+                        double mu_al = g->mu_c + (F * ze + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                        target = eta0 + gen_al_term(&GL, h->cal_true, ccd, gate, day, fi, mu_al) - eps;
+                    }
                     e = remainder(ph - f * 0.5 * g->gamma_c, 2.0 * SIM_PI) - target;
                     if (it > 0 && fabs(o - o_prev) > 10.0) {
                         double sl = (e - e_prev) / (o - o_prev);
@@ -641,7 +736,10 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
                     o_prev = o; e_prev = e;
                     o += -e / slope;
                     int64_t d2 = day_of(c, g, base + (int64_t)llround(o));
-                    if (d2 != day) { day = d2; target = eta0 + h->cal_true[cal_index_al(g, day, fi, ccd)] - eps; }
+                    if (d2 != day) {
+                        day = d2;
+                        if (!generic) target = eta0 + h->cal_true[cal_index_al(g, day, fi, ccd)] - eps;
+                    }
                 }
                 (void)converged;
                 o_last = o; eta0_last = eta0; have_last = 1;
@@ -650,11 +748,17 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
                 /* realised residual at truth after rounding to ns */
                 field_angles(g, dt, coef, &sg, tl, 0.0, &ph, &ze);
                 int64_t dd = day_of(c, g, tl);
-                double tgt_noiseless = eta0 + h->cal_true[cal_index_al(g, dd, fi, ccd)];
+                double mu_rec = 0.0, tgt_noiseless;
+                if (generic) {
+                    mu_rec = g->mu_c + (F * ze + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                    tgt_noiseless = eta0 + gen_al_term(&GL, h->cal_true, ccd, gate, dd, fi, mu_rec);
+                } else {
+                    tgt_noiseless = eta0 + h->cal_true[cal_index_al(g, dd, fi, ccd)];
+                }
                 double eta_l = remainder(ph - f * 0.5 * g->gamma_c, 2.0 * SIM_PI);
                 double R = tgt_noiseless - eta_l;
                 (void)e;
-                buf_push(ob, tl, (int32_t)i, ccd, fi, 0, (float)sig_al, 0.0, R);
+                buf_push(ob, tl, (int32_t)i, ccd, fi, 0, (float)sig_al, mu_rec, R, gate);
                 if (s == 0) t_af1 = tl;
             }
             /* one AC observation on AF1 of the row */
@@ -668,14 +772,27 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
                         eps += (rng_uniform(&rn) < 0.5 ? -1.0 : 1.0) * c->outlier_nsigma * sig_ac;
                 }
                 int64_t dd = day_of(c, g, t_af1);
-                double dz = h->cal_true[cal_index_ac(g, dd, fi, row)];
-                /* zeta0(mu) = zeta - dzeta + eps */
-                double z0 = ze - dz + eps;
-                double mu = g->mu_c + (F * z0 + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                const int gate = gen_gate(c, h->src_mag[i], &rg);
+                double dz, mu;
+                if (generic) {
+                    /* zeta0(mu) + Dzeta(mu) = zeta + eps, solved for mu by fixed-point steps (the
+                     * calibration term changes by < 1e-6 of zeta0's slope per pixel) */
+                    mu = g->mu_c + (F * (ze + eps) + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                    for (int it = 0; it < 4; it++) {
+                        dz = gen_ac_term(&GL, h->cal_true, ccd, gate, dd, fi, mu);
+                        mu = g->mu_c + (F * (ze - dz + eps) + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                    }
+                    dz = gen_ac_term(&GL, h->cal_true, ccd, gate, dd, fi, mu);
+                } else {
+                    dz = h->cal_true[cal_index_ac(g, dd, fi, row)];
+                    /* zeta0(mu) = zeta - dzeta + eps */
+                    double z0 = ze - dz + eps;
+                    mu = g->mu_c + (F * z0 + g->x_fpa[ccd] - g->x_centre[fi]) / g->p_ac;
+                }
                 /* realised residual */
                 double z0r = -(g->x_fpa[ccd] - (mu - g->mu_c) * g->p_ac - g->x_centre[fi]) / F;
                 double R = z0r + dz - ze;
-                buf_push(ob, t_af1, (int32_t)i, ccd, fi, 1, (float)sig_ac, mu, R);
+                buf_push(ob, t_af1, (int32_t)i, ccd, fi, 1, (float)sig_ac, mu, R, gate);
             }
         }
     }
@@ -685,6 +802,96 @@ static void gen_source(sim_handle *h, int64_t i, obs_buf *ob, int32_t *n_transit
 /* ------------------------------------------------------------------------ */
 /* public API                                                                */
 /* ------------------------------------------------------------------------ */
+/* truth of the full geometric calibration: large-scale AL terms N(0, cal_al_rms) for r = 0 and
+ * N(0, cal_l12_rms) for r = 1, 2; small-scale AL terms N(0, cal_small_rms); AC terms on the AF1
+ * CCD of each row (the only ones observed across scan) N(0, cal_ac_rms) for r = 0 and
+ * N(0, cal_l12_rms) for r = 1, 2.  Made to satisfy the constraints: Eq. cc2 per (CCD, gate,
+ * long interval) by removing the least-squares quadratic in the column-centre Legendre values,
+ * Eq. cc1 per day over the r = 0 ungated AL terms, Eq. cc3 per field and long interval over the
+ * r = 0 ungated AC terms. */
+static void gen_truth(sim_handle *h) {
+    const sim_config *cfg = &h->cfg;
+    const gen_layout L = gen_layout_of(cfg, &h->geo);
+    h->n_cal = L.n_al + 6 * L.n_groups;
+    h->cal_true = calloc(h->n_cal, sizeof(double));
+    double *cal = h->cal_true;
+    rng_t r;
+    rng_seed(&r, cfg->seed, 0xCA1ULL, 1);
+    for (int n = 0; n < SIM_NCCD; n++)
+        for (int gt = 0; gt < L.n_gate; gt++)
+            for (int64_t j = 0; j < L.n_j; j++)
+                for (int f = 0; f < 2; f++)
+                    for (int rr = 0; rr < 3; rr++)
+                        cal[gen_deta(&L, n, gt, j, f, rr)] = (rr == 0 ? cfg->cal_al_rms : cfg->cal_l12_rms) * rng_gauss(&r);
+    /* cc2 weights: sum over each bin's columns of L*_r at the column centres */
+    double *w = calloc(3 * L.n_bin, sizeof(double));
+    for (int m = 0; m < SIM_NCOL; m++) {
+        double l[3];
+        gen_legendre(m + 14.0, l);
+        for (int rr = 0; rr < 3; rr++) w[rr * L.n_bin + m / L.col_bin] += l[rr];
+    }
+    double Gm[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double v = 0;
+            for (int64_t k = 0; k < L.n_bin; k++) v += w[a * L.n_bin + k] * w[b * L.n_bin + k];
+            Gm[a][b] = v;
+        }
+    for (int n = 0; n < SIM_NCCD; n++)
+        for (int gt = 0; gt < L.n_gate; gt++)
+            for (int64_t k = 0; k < L.n_k; k++) {
+                double *v = &cal[gen_small(&L, n, gt, k, 0)];
+                for (int64_t b = 0; b < L.n_bin; b++) v[b] = cfg->cal_small_rms * rng_gauss(&r);
+                /* alpha = (W W')^-1 W v by Gaussian elimination on the 3x3 system, v -= W' alpha */
+                double A[3][4];
+                for (int a = 0; a < 3; a++) {
+                    double t = 0;
+                    for (int64_t b = 0; b < L.n_bin; b++) t += w[a * L.n_bin + b] * v[b];
+                    for (int c2 = 0; c2 < 3; c2++) A[a][c2] = Gm[a][c2];
+                    A[a][3] = t;
+                }
+                for (int p = 0; p < 3; p++)
+                    for (int q = p + 1; q < 3; q++) {
+                        double fct = A[q][p] / A[p][p];
+                        for (int c2 = p; c2 < 4; c2++) A[q][c2] -= fct * A[p][c2];
+                    }
+                double al[3];
+                for (int p = 2; p >= 0; p--) {
+                    double t = A[p][3];
+                    for (int q = p + 1; q < 3; q++) t -= A[p][q] * al[q];
+                    al[p] = t / A[p][p];
+                }
+                for (int64_t b = 0; b < L.n_bin; b++)
+                    v[b] -= al[0] * w[b] + al[1] * w[L.n_bin + b] + al[2] * w[2 * L.n_bin + b];
+            }
+    free(w);
+    for (int n = 0; n < SIM_NCCD; n++) {
+        if (h->geo.ccd_strip[n] != 0) continue;
+        for (int gt = 0; gt < L.n_gate; gt++)
+            for (int64_t k = 0; k < L.n_k; k++)
+                for (int f = 0; f < 2; f++)
+                    for (int rr = 0; rr < 3; rr++)
+                        cal[gen_dzeta(&L, n, gt, k, f, rr)] = (rr == 0 ? cfg->cal_ac_rms : cfg->cal_l12_rms) * rng_gauss(&r);
+    }
+    for (int64_t j = 0; j < L.n_j; j++) {
+        double m = 0;
+        for (int f = 0; f < 2; f++)
+            for (int n = 0; n < SIM_NCCD; n++) m += cal[gen_deta(&L, n, 0, j, f, 0)];
+        m /= 2 * SIM_NCCD;
+        for (int f = 0; f < 2; f++)
+            for (int n = 0; n < SIM_NCCD; n++) cal[gen_deta(&L, n, 0, j, f, 0)] -= m;
+    }
+    for (int64_t k = 0; k < L.n_k; k++)
+        for (int f = 0; f < 2; f++) {
+            double m = 0;
+            for (int n = 0; n < SIM_NCCD; n++)
+                if (h->geo.ccd_strip[n] == 0) m += cal[gen_dzeta(&L, n, 0, k, f, 0)];
+            m /= SIM_NROW;
+            for (int n = 0; n < SIM_NCCD; n++)
+                if (h->geo.ccd_strip[n] == 0) cal[gen_dzeta(&L, n, 0, k, f, 0)] -= m;
+        }
+}
+
 sim_handle *sim_create(const sim_config *cfg) {
     sim_handle *h = calloc(1, sizeof(sim_handle));
     h->cfg = *cfg;
@@ -721,6 +928,10 @@ sim_handle *sim_create(const sim_config *cfg) {
     }
     /* calibration truth, projected onto the constraints Eq. cc1 and cc3 */
     int64_t nd = h->geo.n_cal_days;
+    if (cfg->cal_generic) {
+        gen_truth(h);
+        return h;
+    }
     h->n_cal = nd * 2 * (SIM_NCCD + SIM_NROW);
     h->cal_true = calloc(h->n_cal, sizeof(double));
     {
@@ -859,6 +1070,26 @@ void sim_copy_obs(const sim_handle *h, int64_t *t_ns, int32_t *src, uint8_t *ccd
     free(off);
 }
 
+/* gates of the kept observations, in the order of sim_copy_obs */
+void sim_copy_gate(const sim_handle *h, uint8_t *gate) {
+    int64_t o = 0;
+    int nt = h->nthreads;
+    int64_t ns = h->cfg.n_src;
+    int64_t chunk = (ns + nt - 1) / nt;
+    for (int tid = 0; tid < nt; tid++) {
+        const obs_buf *b = &h->bufs[tid];
+        int64_t j = 0;
+        int64_t i0 = tid * chunk, i1 = i0 + chunk;
+        if (i1 > ns) i1 = ns;
+        for (int64_t i = i0; i < i1; i++) {
+            int64_t c = h->src_count[i];
+            if (h->keep[i])
+                for (int64_t k = 0; k < c; k++) gate[o++] = b->gate[j + k];
+            j += c;
+        }
+    }
+}
+
 /* truth and starting values */
 void sim_copy_truth(const sim_handle *h, double *src_true, double *src_mag, double *att_true, double *cal_true,
                     int32_t *n_transits) {
@@ -934,7 +1165,7 @@ void sim_destroy(sim_handle *h) {
         for (int t = 0; t < h->nthreads; t++) {
             obs_buf *b = &h->bufs[t];
             free(b->t_ns); free(b->src); free(b->ccd); free(b->fov); free(b->kind);
-            free(b->sigma); free(b->mu); free(b->noise);
+            free(b->sigma); free(b->mu); free(b->noise); free(b->gate);
         }
         free(h->bufs);
     }

@@ -290,3 +290,58 @@ def test_zero_point_constraints_cover_the_nongated_offsets():
     idx += [L.dzeta_large(n, g, k, f, r) for n in range(4) for g in range(3) for k in range(2) for f in (0, 1)
             for r in range(3)]
     assert sorted(int(i) for i in idx) == list(range(L.n_params))
+
+
+# --- the generic model through the oracle's observation model and C block, on generated data
+
+import pytest  # noqa: E402
+
+import synth  # noqa: E402
+from oracle import blocks as OB  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def generic_ds():
+    # noise-free, 40k sources over 30 days: 2 gates (G + N(0, 0.15) below 13 gated), one
+    # 30-day long interval, 10 column bins; ~5.4e5 observations, every (CCD, gate) group
+    # determined
+    return synth.simulate(synth.config("small1yr", n_src=40_000, span_days=30, seed=11, noise_free=True,
+                                       cal_generic=True, n_gate=2, cal_j_per_k=30, cal_col_bin=197))
+
+
+def test_generated_data_follow_the_generic_model(generic_ds):
+    # the residuals of the oracle's model at the truth are the generator's realised noise (here
+    # the rounding of the times to ns), so the two implementations of Eq. etazeta agree; the
+    # data carry gated observations, sources seen with both gates, AL pixel coordinates
+    ds = generic_ds
+    P = OM.problem_from_dataset(ds)
+    assert P.calg is not None and P.n_cal == ds.n_cal
+    R = OM.evaluate(P, ds.src_true, ds.att_true, ds.cal_true, partials=False)["R"]
+    assert np.all(np.abs(R - ds.noise) <= 1e-9 * np.abs(ds.noise) + 1e-15)
+    assert 0.05 < np.mean(ds.gate > 0) < 0.5
+    lo = np.full(ds.n_src, 9)
+    hi = np.zeros(ds.n_src, int)
+    np.minimum.at(lo, ds.src, ds.gate)
+    np.maximum.at(hi, ds.src, ds.gate)
+    assert np.sum(lo != hi) > 500
+    al = ds.kind == 0
+    assert ds.mu[al].min() > 14.0 and ds.mu[al].max() < 1979.0
+
+
+def test_one_calibration_update_recovers_the_truth(generic_ds):
+    # sources and attitude at the truth, calibration from zero: one C update (Sect. 5.3) gives
+    # back the truth to the noise of the data (|noise| <= 0.05 uas from the ns rounding): every
+    # observed parameter, the residuals, and the basic angle of every day
+    ds = generic_ds
+    P = OM.problem_from_dataset(ds)
+    ev = OM.evaluate(P, ds.src_true, ds.att_true, np.zeros(ds.n_cal))
+    W = 1.0 / ds.sigma.astype(np.float64) ** 2
+    cal1, rd = OB.calibration_update(P, np.zeros(ds.n_cal), ev, ev["R"], W)
+    noise = np.abs(ds.noise).max()
+    Nal, _, Nac, _ = G.group_normals(P.calg, ev["cal_cols"], ev["cal_vals"], ev["R"], W)
+    obs = np.r_[np.concatenate([np.diagonal(N) for N in Nal]), np.concatenate([np.diagonal(N) for N in Nac])] > 0
+    assert rd == np.sum(~obs)                       # the only rank defects: unobserved parameters
+    assert np.abs(cal1 - ds.cal_true)[obs].max() < 2 * noise
+    R1 = OM.evaluate(P, ds.src_true, ds.att_true, cal1, partials=False)["R"]
+    assert np.abs(R1).max() < 2 * noise
+    assert np.abs(G.delta_gamma(P.calg, cal1) - G.delta_gamma(P.calg, ds.cal_true)).max() < noise
