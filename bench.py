@@ -156,7 +156,7 @@ def load_peaks():
         return {}
 
 
-# Algorithmic FP64 operations per observation of the S pass ("Roofline"):
+# Algorithmic FP64 operations per observation of the S pass (the FP64 form's roofline):
 # forward model 160, partials 60, robust sigma 10, 5 normal-equation passes x 26 and
 # 5 residual passes x 12, hand-over 10.  Transcendentals (sincos, atan2, sqrt, exp, div)
 # count as one operation each.
