@@ -98,6 +98,18 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x, dist):
+    """The largest x over the ranks (the whole job's time is its slowest replica's); x itself
+    when there is no process group.  NCCL reduces a device tensor, gloo a host one."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -288,9 +300,7 @@ def time_form(agis, ds, stream, cfg, steps, warmup, local, dist, tune_iters=0, a
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / steps
     if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, dist)
     g.close()
     full = [it for it in its if it["s"]["full_eval"]]
     lin = [it for it in its if not it["s"]["full_eval"]]
