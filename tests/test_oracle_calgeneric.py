@@ -345,3 +345,28 @@ def test_one_calibration_update_recovers_the_truth(generic_ds):
     R1 = OM.evaluate(P, ds.src_true, ds.att_true, cal1, partials=False)["R"]
     assert np.abs(R1).max() < 2 * noise
     assert np.abs(G.delta_gamma(P.calg, cal1) - G.delta_gamma(P.calg, ds.cal_true)).max() < noise
+
+
+def test_constrained_solve_over_random_layouts():
+    # random group shapes (short intervals per long one, columns, bin width) and random data:
+    # the null-space solution equals the balanced KKT solve and satisfies cc2
+    for seed in range(12):
+        rng = np.random.default_rng(100 + seed)
+        nj = int(rng.integers(1, 4))
+        L = G.Layout(n_ccd=1, n_gate=1, n_j=nj, j_per_k=nj, n_col=int(rng.integers(6, 21)),
+                     col_bin=int(rng.integers(1, 4)))
+        n = 200 * L.al_size
+        kind, fov, ccd, gate, j, mu = _obs(L, n, rng, ac_frac=0.0)
+        cols, vals = G.design(L, kind, fov, ccd, gate, j, mu)
+        R = rng.normal(size=n) * 1e-9
+        W = rng.uniform(0.2, 5.0, n) * 1e16
+        Nal, bal, _, _ = G.group_normals(L, cols, vals, R, W)
+        N, b = Nal[0], bal[0]
+        C2 = G.cc2_matrix(L)
+        x, rd = G.constrained_solve(N, b, C2)
+        sc = np.sqrt(np.trace(N) / L.al_size)
+        K = np.block([[N, sc * C2], [sc * C2.T, np.zeros((3, 3))]])
+        xk = np.linalg.solve(K, np.concatenate([b, np.zeros(3)]))[:L.al_size]
+        assert rd == 0, (seed, rd)
+        assert np.abs(x - xk).max() < 1e-8 * np.abs(xk).max(), seed
+        assert np.abs(C2.T @ x).max() < 1e-12 * np.abs(x).max() * L.n_col, seed
