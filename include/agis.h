@@ -352,7 +352,8 @@ int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, 
  * (precision 0), block orders S[AC] and SAC, not together with ASI or the learned proposal.
  * Errors: AGIS_E_INVALID (bucket_ns < 0, one of those combinations, an observation before
  * knot0_ns, more than 2^30 / 3 buckets), AGIS_E_OOM, AGIS_E_CUDA.  Device memory: 20 bytes
- * per observation and 32 bytes per bucket, owned by the context. */
+ * per observation and 48 bytes per bucket, owned by the context (and 12 bytes per
+ * observation during this call, for the sort of the (component, bucket) order). */
 int agis_set_attnoise(agis_ctx* ctx, int64_t bucket_ns);
 /* *n_buckets = the number of buckets (0 when the noise is off); if eps2_a is not NULL and
  * the noise is on, eps2_a[c * n_buckets + j] = eps_a^2 of component c (0 AL, 1 AC preceding
