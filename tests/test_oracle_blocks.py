@@ -9,6 +9,7 @@ from oracle import agis as G
 from oracle import blocks as B
 from oracle import model as M
 from oracle import quat as Q
+from oracle import weights as WF
 
 UAS = synth.UAS
 
@@ -291,3 +292,28 @@ def test_rigorous_transform_agrees_with_linear_form(small_noisefree):
     _, _, r1 = M.normal_triad(out[:, 0], out[:, 1])
     lin = r + np.cross(r, np.broadcast_to(eps, r.shape))   # Eq. fr3 with t = t_fr
     assert np.max(np.linalg.norm(r1 - lin, axis=1)) < 0.002 * UAS
+
+
+def test_source_statistics_against_the_noise():
+    # Gaussian noise without outliers, sources updated from the truth (attitude and calibration
+    # at the truth): (1) the formal covariances describe the errors, the robust scale estimate
+    # of the normalised errors (0.390152 x the 10-90% range, the RSE of the paper's tables) is
+    # 1 within its sampling error; (2) Q0 = sum w R^2 / sigma^2 with the weights of Eq. dw, which
+    # already fall below 1 beyond |z| = 2, has the expectation nu E[w(z) z^2] for standard
+    # normal z (about 0.93 nu, not nu): the mean of Q0 / nu over the sources, from
+    # D = (Q0 - nu) / sqrt(2 nu), against that expectation by quadrature
+    from scipy import integrate
+    from scipy.stats import norm
+    ds = synth.simulate(synth.config("small1yr", n_src=2000, seed=31, outlier_frac=0.0, min_transits=8))
+    P = M.problem_from_dataset(ds)
+    src1, sres, _ = B.source_update(P, ds.src_true, ds.att_true, ds.cal_true, B.Settings(seg_len=720))
+    z = G.source_errors(src1, ds.src_true) / np.sqrt(np.einsum("ikk->ik", sres.cov))
+    rse = 0.390152 * (np.quantile(z, 0.9, axis=0) - np.quantile(z, 0.1, axis=0))
+    assert np.all(np.abs(rse - 1.0) < 0.08), rse          # sampling error of the RSE ~0.025 here
+    ok = sres.nu > 20
+    q0nu = 1.0 + sres.D[ok] * np.sqrt(2.0 / sres.nu[ok])
+    wz2 = lambda t: WF.w_agis(t) * t * t * norm.pdf(t)  # noqa: E731
+    expect = 2.0 * sum(integrate.quad(wz2, lo, hi, epsabs=1e-13)[0] for lo, hi in ((0, 2), (2, 3), (3, 40)))
+    se = q0nu.std() / np.sqrt(ok.sum())
+    assert 0.92 < expect < 0.94
+    assert abs(q0nu.mean() - expect) < 4 * se, (q0nu.mean(), expect, se)
