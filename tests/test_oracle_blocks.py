@@ -317,3 +317,27 @@ def test_source_statistics_against_the_noise():
     se = q0nu.std() / np.sqrt(ok.sum())
     assert 0.92 < expect < 0.94
     assert abs(q0nu.mean() - expect) < 4 * se, (q0nu.mean(), expect, se)
+
+
+def test_attitude_normals_without_the_norm_term_are_singular_along_the_coefficients():
+    # Sect. 5.2.3: the observations see only q = s / |s|, so scaling every coefficient of a
+    # segment changes no residual and the normals from the observations alone have exactly one
+    # null direction, the coefficient vector itself; the lambda^2 term of Eq. JfuncMod lifts it
+    from oracle import cholesky as CH
+    ds = synth.simulate(synth.config("small1yr", n_src=3000, seed=21))
+    P = M.problem_from_dataset(ds)
+    l_lo, l_hi = 500, 547                                  # 48 knot intervals, 51 coefficients
+    kn = P.knots()
+    sel = np.nonzero((ds.t_ns >= kn[l_lo]) & (ds.t_ns < kn[l_hi + 1]))[0]
+    ev = M.evaluate(P, ds.src_true, ds.att_true, ds.cal_true, idx=sel)
+    W = 1.0 / P.sigma[sel].astype(np.float64) ** 2
+    a = ds.att_true[l_lo - 3:l_hi + 1].ravel()
+    for lam in (0.0, 1e-3):
+        Nb, _ = B.attitude_normals(P, ev, ev["R"], W, B.Settings(seg_len=720, lam=lam), l_lo, l_hi)
+        N = CH.band_to_dense(Nb)
+        e = np.linalg.eigvalsh(N) / np.linalg.eigvalsh(N)[-1]
+        if lam == 0.0:
+            assert e[0] < 1e-15 and e[1] > 1e-13
+            assert np.linalg.norm(N @ a) < 1e-14 * np.linalg.norm(N, 2) * np.linalg.norm(a)
+        else:
+            assert e[0] > 1e-11
