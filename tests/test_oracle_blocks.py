@@ -341,3 +341,30 @@ def test_attitude_normals_without_the_norm_term_are_singular_along_the_coefficie
             assert np.linalg.norm(N @ a) < 1e-14 * np.linalg.norm(N, 2) * np.linalg.norm(a)
         else:
             assert e[0] > 1e-11
+
+
+def test_first_source_update_hardly_depends_on_the_starting_sources():
+    # The source update is independent of the current source values (Sect. 4.5, the footnote
+    # on the zero columns of the iteration matrix) up to what a Gauss-Newton step keeps of its
+    # starting point: second order in
+    # the offset through the model's curvature (positions: halving the offset quarters the
+    # difference) and first order through the aberration-level approximation of the partials
+    # (Eq. duds; parallax and proper motions: halving halves it).  From the demonstration's
+    # starting values (50 mas, zero parallax and proper motion) the update lands within 1 uas
+    # of the one started at the truth; noise-free data, attitude and calibration at the truth.
+    ds = synth.simulate(synth.config("small1yr", n_src=500, seed=41, min_transits=8, noise_free=True))
+    P = M.problem_from_dataset(ds)
+    st = B.Settings(seg_len=720, robust=False)
+    rng = np.random.default_rng(0)
+    off = np.column_stack([rng.normal(size=(ds.n_src, 2)) * 50 * synth.MAS, -ds.src_true[:, 2:]])
+    out = {}
+    for scale in (0.0, 0.5, 1.0):
+        s0 = ds.src_true.copy()
+        s0[:, 0] += scale * off[:, 0] / np.cos(s0[:, 1])
+        s0[:, 1] += scale * off[:, 1]
+        s0[:, 2:] += scale * off[:, 2:]
+        out[scale], _, _ = B.source_update(P, s0, ds.att_true, ds.cal_true, st)
+    full = np.abs(G.source_errors(out[1.0], out[0.0])).max(axis=0)
+    half = np.abs(G.source_errors(out[0.5], out[0.0])).max(axis=0)
+    assert np.all(full < 1.0 * UAS), full / UAS
+    assert np.all(half < 0.6 * full), half / full
