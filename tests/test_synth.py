@@ -43,3 +43,15 @@ def test_magnitude_dependent_sigma():
                                      max_transits=0))
     s_al = ds.sigma[ds.kind == 0].astype(float) / synth.UAS
     assert 45 < s_al.min() and s_al.max() < 520
+
+
+def test_independent_of_the_thread_count_in_both_calibration_modes():
+    # every source draws from its own counter-based stream (and the gates from a stream of
+    # their own), so the data do not depend on how the sources are split among threads
+    fields = ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu", "noise", "gate", "cal_true", "att_true", "src0")
+    for extra in ({}, dict(cal_generic=True, n_gate=3, cal_j_per_k=5, cal_col_bin=131)):
+        a = synth.simulate(synth.config("small1yr", n_src=1500, span_days=20, seed=3, n_threads=1, **extra))
+        b = synth.simulate(synth.config("small1yr", n_src=1500, span_days=20, seed=3, n_threads=4, **extra))
+        assert a.n_obs > 1000
+        for f in fields:
+            assert np.array_equal(getattr(a, f), getattr(b, f)), (extra, f)
