@@ -395,3 +395,32 @@ def test_truth_is_a_fixed_point_of_the_whole_iteration():
     s2 = max(np.abs(G.cc2_matrix(P.calg).T @ new.cal[g * P.calg.al_size:(g + 1) * P.calg.al_size]).max()
              for g in range(P.calg.n_groups))
     assert s2 < 1e-12 * np.abs(new.cal).max() * P.calg.n_col
+
+
+def test_block_elimination_gives_the_same_constrained_solution():
+    # An independent route to a group's constrained least-squares solution: eliminate each
+    # short interval's 6x6 block of large-scale terms (the Schur complement onto the
+    # small-scale terms), impose cc2 on the reduced system (it acts on the small-scale terms
+    # alone), back-substitute.  Equal to the oracle's dense null-space solve.
+    import scipy.linalg as sl
+    L = G.Layout(n_ccd=1, n_gate=1, n_j=4, j_per_k=4, n_col=30, col_bin=2)
+    rng = np.random.default_rng(11)
+    kind, fov, ccd, gate, j, mu = _obs(L, 6000, rng, ac_frac=0.0)
+    cols, vals = G.design(L, kind, fov, ccd, gate, j, mu)
+    Nal, bal, _, _ = G.group_normals(L, cols, vals, rng.normal(size=6000) * 1e-9, rng.uniform(0.5, 2, 6000) * 1e16)
+    N, b = Nal[0], bal[0]
+    C2 = G.cc2_matrix(L)
+    x, rd = G.constrained_solve(N, b, C2)
+    big = [np.arange(6 * k, 6 * k + 6) for k in range(L.j_per_k)]
+    sm = np.arange(6 * L.j_per_k, L.al_size)
+    S = N[np.ix_(sm, sm)].copy()
+    bs = b[sm].copy()
+    for J in big:
+        Bj, Cj = N[np.ix_(J, J)], N[np.ix_(J, sm)]
+        S -= Cj.T @ np.linalg.solve(Bj, Cj)
+        bs -= Cj.T @ np.linalg.solve(Bj, b[J])
+    Z = sl.null_space(C2[sm].T)
+    v = Z @ np.linalg.solve(Z.T @ S @ Z, Z.T @ bs)
+    u = [np.linalg.solve(N[np.ix_(J, J)], b[J] - N[np.ix_(J, sm)] @ v) for J in big]
+    xe = np.concatenate(u + [v])
+    assert rd == 0 and np.abs(x - xe).max() < 1e-9 * np.abs(xe).max()
