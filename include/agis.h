@@ -199,7 +199,10 @@ int agis_get_calibration(agis_ctx* ctx, double* cal_out);       /* n_cal */
 int agis_set_sources(agis_ctx* ctx, const double* src);
 int agis_set_attitude(agis_ctx* ctx, const double* att);
 int agis_set_calibration(agis_ctx* ctx, const double* cal);
-/* Residuals and weights handed from the latest S block to A and C (caller order). */
+/* Residuals and weights handed from the latest S block to A and C (caller order): available
+ * after any source update until a state is set (a frame rotation leaves them as they are; in
+ * block order 1 they include the first-order attitude correction that the C block read).
+ * AGIS_E_INVALID before the first source update or after an agis_set_* call. */
 int agis_get_residuals(agis_ctx* ctx, double* R_out, double* W_out);
 /* Per-source results of the latest S block: eps_i^2, Q_i, nu_i, n_out_i, D_i (5 x n_src doubles,
  * row-major by quantity) and the 5x5 inverse normal matrices (n_src x 25 doubles, or NULL). */
@@ -234,8 +237,12 @@ int agis_abi_version(void);
  * The first call on a device looks up the array's device address with that device current;
  * make it before any stream capture.  All calls share the array and it keeps the last
  * call's contents: calls that overlap on the GPU race and must be serialised.  Errors:
- * AGIS_E_INVALID (bad arguments, or a source with more than max_obs_per_source observations;
- * message in agis_last_error(NULL)), AGIS_E_CUDA.  Synchronises the stream before returning. */
+ * AGIS_E_INVALID for bad arguments, and for inputs that a check kernel finds before anything
+ * is written (source index out of range, sources not sorted, ccd, fov or kind out of range,
+ * sigma not positive and finite, non-finite mu of an AC observation, non-finite src, att or
+ * cal, a source with more than max_obs_per_source observations): src and the outputs are
+ * then unchanged; the message is in agis_last_error(NULL).  AGIS_E_CUDA.  Synchronises the
+ * stream before returning (twice: after the check and after the update). */
 int agis_source_update_static(const agis_geometry* geo, const agis_config* cfg, const agis_obs* obs, int64_t n_obs,
                               double* src, int32_t n_src, const double* att, const double* cal, double* R_out,
                               double* W_out, double* stats_out, int32_t max_obs_per_source, void* stream);

@@ -287,6 +287,7 @@ struct agis_ctx {
     double* hstat = nullptr;      // 10 S, 6 frame at 16, 4 ASI estimate at 24
     long long* hisum = nullptr;   // 2
     bool have_s = false;
+    bool have_s_out = false;    // the S block's hand-over (R, W) exists and no state was set since
     bool a_since_c = false;     // an A update not yet seen by a C update (block Gauss-Seidel)
     static constexpr int kEvents = 14;
     cudaEvent_t ev[kEvents];
@@ -788,12 +789,14 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         cuda_check(c, cudaStreamSynchronize(s), "validate (sync)"))
         return bail(AGIS_E_CUDA);
     if (herr) {
-        char buf[200];
-        std::snprintf(buf, sizeof(buf),
-                      "invalid input (flags 0x%x: 1 source index out of range, 2 not sorted by source, "
-                      "4 ccd/fov/kind out of range, 8 sigma not positive, 16 mu not finite, 32 non-finite state)",
-                      herr);
-        return bail(fail(c, AGIS_E_INVALID, buf));
+        static const char* what[6] = {"source index out of range", "observations not sorted by source",
+                                      "ccd, fov or kind out of range", "sigma not positive and finite",
+                                      "mu of an AC observation not finite",
+                                      "non-finite starting value (src0, att0 or cal0)"};
+        std::string msg = "invalid input:";
+        for (int b = 0; b < 6; b++)
+            if (herr & (1 << b)) msg += std::string(" ") + what[b] + ";";
+        return bail(fail(c, AGIS_E_INVALID, msg));
     }
     // ---- internal order: by source, AL before AC (the per-class passes of the S block then
     // sweep contiguous ranges)
@@ -957,6 +960,7 @@ int agis_source_update(agis_ctx* c, agis_block_stats* out) {
     s_done(c, refresh);
     c->hist_count++;
     c->have_s = true;
+    c->have_s_out = true;
     c->a_since_c = false;   // the source update reset the attitude update C would see
     fill_s_stats(c, c->hstat, out);
     c->ktimes[0] = elapsed(c, 0, 1);
@@ -1172,7 +1176,10 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             AGIS_CU(c, cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                     "stats");
         AGIS_CU(c, cudaStreamSynchronize(c->stream), "iteration");
-        if (mask & 1) c->have_s = !do_frame;
+        if (mask & 1) {
+            c->have_s = !do_frame;
+            c->have_s_out = true;
+        }
         c->a_since_c = false;
         if (per_iter) {
             agis_iter_stats& it = per_iter[k];
@@ -1229,6 +1236,7 @@ static int set_copy(agis_ctx* c, void* dst, const void* src, size_t bytes) {
     AGIS_CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy");
     AGIS_CU(c, cudaStreamSynchronize(c->stream), "copy (sync)");
     c->have_s = false;
+    c->have_s_out = false;
     c->mix_stale = true;
     c->hist_count = 0;
     c->prop_pending = false;
@@ -1242,7 +1250,7 @@ int agis_set_calibration(agis_ctx* c, const double* v) { return c ? set_copy(c, 
 
 int agis_get_residuals(agis_ctx* c, double* R_out, double* W_out) {
     if (!c) return AGIS_E_INVALID;
-    if (!c->have_s) return fail(c, AGIS_E_INVALID, "no source update since the last state change");
+    if (!c->have_s_out) return fail(c, AGIS_E_INVALID, "no source update since the last state change");
     if (!c->tmpR) AGIS_TRY(dalloc(c, &c->tmpR, (size_t)c->n_obs));
     if (!c->tmpW) AGIS_TRY(dalloc(c, &c->tmpW, (size_t)c->n_obs));
     if (c->mixed)

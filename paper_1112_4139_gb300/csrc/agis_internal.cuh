@@ -239,6 +239,24 @@ __device__ __forceinline__ double dkey_inv(uint64_t k) {
 // Excess attitude noise (Sect. 5.2.5): eps_a^2 of the three components (AL, AC in the
 // preceding field, AC in the following field) per time bucket [t0 + j dt, t0 + (j+1) dt),
 // stored eps2[comp * n_b + j].  eps2 null: off.
+// 1/d for d > 0 by Newton's iteration for the reciprocal, y <- y + y (1 - d y), two steps
+// from an FP32 seed (rcp.approx of d rounded to FP32).  The seed's relative error e0 (below
+// 2^-22: the FP32 rounding of d plus the approximate reciprocal) becomes e0^2 after one step
+// and e0^4 < 2^-88 after two, so the result differs from 1/d by the rounding of the last
+// FMA: at most one FP64 ulp (the GPU unit test measures the largest difference from the
+// correctly rounded 1.0 / d over random and edge values).  d outside [2^-100, 2^101)
+// (exponent bits) takes the plain division.
+__device__ __forceinline__ double rcp_pos(double d) {
+    const int ex = (__double2hiint(d) >> 20) & 0x7ff;
+    if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(__double2float_rn(d)));
+    double y = (double)y0;
+    y = fma(y, fma(-d, y, 1.0), y);
+    y = fma(y, fma(-d, y, 1.0), y);
+    return y;
+}
+
 struct AttNoise {
     const double* eps2 = nullptr;
     int64_t t0 = 0, dt = 1;

@@ -238,21 +238,6 @@ __device__ __forceinline__ void cp_async_wait_att() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// 1/d for d > 0 by two Newton-Raphson steps y <- y + y (1 - d y) from an FP32 seed: the
-// seed's relative error (below 2^-22: FP32 rounding of d and the approximate reciprocal) is
-// squared by each step, so the result is within the FP64 rounding of 1/d.  d outside
-// [2^-100, 2^100] (checked on the exponent bits) takes the plain division.
-__device__ __forceinline__ double rcp_pos(double d) {
-    const int ex = (__double2hiint(d) >> 20) & 0x7ff;
-    if (ex < 1023 - 100 || ex > 1023 + 100) return 1.0 / d;
-    float y0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(__double2float_rn(d)));
-    double y = (double)y0;
-    y = fma(y, fma(-d, y, 1.0), y);
-    y = fma(y, fma(-d, y, 1.0), y);
-    return y;
-}
-
 __device__ __forceinline__ double& win(SegWin& sm, int row, int col) {
     return sm.Wf[row * 16 + ((col + row) & 15)];
 }

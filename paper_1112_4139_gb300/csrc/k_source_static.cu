@@ -2,11 +2,10 @@
 //
 // Some callers cannot allocate device memory: code running where the allocator is owned by
 // someone else (a host framework with its own pool, or a process that has reserved all
-// device memory up front), or a caller that must not allocate between two graph captures.
-// agis_source_update_static() runs the same source update as agis_source_update() on
-// caller-owned device arrays.  The only scratch it needs lives in the file-scope device
-// array below: every GPU that loads this library keeps those 32 MiB until the process
-// exits.
+// device memory up front).  agis_source_update_static() runs the same source update as
+// agis_source_update() on caller-owned device arrays.  The only scratch it needs lives in
+// the file-scope device array below: every GPU that loads this library keeps those 32 MiB
+// until the process exits.
 //
 // Rules for callers:
 //  * The first call on a device looks up the device address of the scratch array
@@ -15,8 +14,13 @@
 //  * All calls share the one array, and it keeps the contents of the last call.  Calls
 //    whose kernels overlap on the GPU (different streams, or different host threads on the
 //    same device) race on it and give wrong results: serialise them.
-//  * Sources with more than max_obs_per_source observations are rejected
-//    (AGIS_E_INVALID); max_obs_per_source must not exceed AGIS_STATIC_MAX_OBS.
+//  * Every call first checks its inputs on the device (source indices in range and sorted,
+//    CCD, field and kind in range, sigma positive and finite, mu finite for AC, finite
+//    parameters, at most max_obs_per_source observations per source) and reads the result
+//    back before the compute kernel starts: on AGIS_E_INVALID no output has been written.
+//    max_obs_per_source must not exceed AGIS_STATIC_MAX_OBS.
+//  * Each call synchronises its stream before it returns (the check result and the
+//    compute kernel's status are read back).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -177,6 +181,35 @@ __device__ void s_q(const double* scr, int n, int lane, const double* d, double 
     S2 = warp_sum(s);
 }
 
+// Input check before any output is written; bits of ctrl[1]: 1 a source with more than cap
+// observations, 2 source index out of range, 4 sources not sorted, 8 CCD, field or kind out of
+// range, 16 sigma not positive and finite, 32 non-finite mu of an AC observation, 64 a
+// non-finite parameter (sources, attitude or calibration).  With sorted sources, observation o
+// and observation o - cap belong to the same source exactly when that source has more than
+// cap observations.
+__global__ void k_static_check(int64_t n_obs, ObsPtrs ob, int32_t n_src, int cap, const double* __restrict__ src,
+                               int64_t n_s, const double* __restrict__ att, int64_t n_a,
+                               const double* __restrict__ cal, int64_t n_c, int* ctrl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += stride) {
+        const int32_t s = ob.src[o];
+        if (s < 0 || s >= n_src) bad |= 2;
+        if (o > 0 && ob.src[o - 1] > s) bad |= 4;
+        if (o >= cap && ob.src[o - cap] == s) bad |= 1;
+        const int k = ob.kind[o];
+        if (ob.ccd[o] >= AGIS_N_CCD || ob.fov[o] > 1 || k > 1) bad |= 8;
+        const float sg = ob.sigma[o];
+        if (!(sg > 0.0f) || !isfinite(sg)) bad |= 16;
+        if (k == 1 && !isfinite(ob.mu[o])) bad |= 32;
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_s + n_a + n_c; j += stride) {
+        const double v = j < n_s ? src[j] : j < n_s + n_a ? att[j - n_s] : cal[j - n_s - n_a];
+        if (!isfinite(v)) bad |= 64;
+    }
+    if (bad) atomicOr(&ctrl[1], bad);
+}
+
 // One warp per source: observation pass into the warp's slice of the static scratch, then the
 // inner iteration of Sect. 5.1.2 (per-observation form) and the outputs.
 __global__ void __launch_bounds__(128) k_source_static(DevGeo G, Settings st, ObsPtrs ob, int64_t n_obs,
@@ -200,8 +233,8 @@ __global__ void __launch_bounds__(128) k_source_static(DevGeo G, Settings st, Ob
         const int64_t o0 = lower_bound_src(ob.src, n_obs, i);
         const int64_t o1 = lower_bound_src(ob.src, n_obs, i + 1);
         const int n = (int)(o1 - o0);
-        if (n > cap) {
-            if (lane == 0) atomicOr(&ctrl[1], 1);
+        if (n < 0 || n > cap) {   // excluded by k_static_check; kept as a guard
+            if (lane == 0) atomicOr(&ctrl[1], n < 0 ? 4 : 1);
             continue;
         }
         double s5[5];
@@ -378,13 +411,36 @@ extern "C" int agis_source_update_static(const agis_geometry* geo, const agis_co
     if (blocks < 1) return err(AGIS_E_INVALID, "max_obs_per_source too large for the static scratch");
     cudaError_t e = cudaMemsetAsync(ctrl, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return err(AGIS_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    // inputs first, read back before anything is written
+    int flags[4] = {0, 0, 0, 0};
+    {
+        const int64_t n_s = 5 * (int64_t)n_src, n_a = 4 * (int64_t)geo->n_coef,
+                      n_c = (int64_t)geo->n_cal_days * (2 * (AGIS_N_CCD + AGIS_N_ROW));
+        const int64_t work = n_obs > n_s + n_a + n_c ? n_obs : n_s + n_a + n_c;
+        int64_t nb = (work + 255) / 256;
+        if (nb > 152 * 8) nb = 152 * 8;
+        if (nb < 1) nb = 1;
+        k_static_check<<<(int)nb, 256, 0, s>>>(n_obs, op, n_src, max_obs_per_source, src, n_s, att, n_a, cal, n_c,
+                                               (int*)ctrl);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(flags, ctrl, sizeof(flags), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return err(AGIS_E_CUDA, std::string("input check: ") + cudaGetErrorString(e));
+        const int b = flags[1];
+        if (b & 2) return err(AGIS_E_INVALID, "source index out of range");
+        if (b & 4) return err(AGIS_E_INVALID, "observations not sorted by source");
+        if (b & 8) return err(AGIS_E_INVALID, "ccd, fov or kind out of range");
+        if (b & 16) return err(AGIS_E_INVALID, "sigma must be positive and finite");
+        if (b & 32) return err(AGIS_E_INVALID, "non-finite mu of an AC observation");
+        if (b & 64) return err(AGIS_E_INVALID, "non-finite source, attitude or calibration parameter");
+        if (b & 1) return err(AGIS_E_INVALID, "a source has more observations than max_obs_per_source");
+    }
     if (n_src > 0)
         k_source_static<<<blocks, 128, 0, s>>>(G, st, op, n_obs, n_src, rows, geo->cal_t0_ns, geo->cal_dt_ns,
                                                geo->n_cal_days, src, att, cal, R_out, W_out, stats_out, cap,
                                                (double*)scratch, (int*)ctrl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(AGIS_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-    int flags[4] = {0, 0, 0, 0};
     e = cudaMemcpyAsync(flags, ctrl, sizeof(flags), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return err(AGIS_E_CUDA, std::string("static source update: ") + cudaGetErrorString(e));
