@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-#define AGIS_ABI_VERSION 7
+#define AGIS_ABI_VERSION 8
 
 #define AGIS_OK 0
 #define AGIS_E_INVALID (-1)    /* bad argument or call order                            */
@@ -34,6 +34,8 @@ extern "C" {
 
 #define AGIS_N_CCD 62          /* astrometric-field CCDs (Sect. 3.4)                    */
 #define AGIS_N_ROW 7           /* across-scan CCD rows                                  */
+#define AGIS_N_COL 1966        /* AC pixel columns of a CCD (Eq. etazeta, small-scale terms) */
+#define AGIS_MAX_GATE 16       /* gates of the full calibration model (g = 0 .. n_gate-1) */
 
 /* Instrument, ephemeris, epochs and knots (Sects. 3.2-3.4). */
 typedef struct agis_geometry {
@@ -77,8 +79,30 @@ typedef struct agis_config {
     int32_t precision;           /* 0: FP64 throughout; 1: mixed (see below)                 */
     int32_t refresh_every;       /* mixed: full FP64 residual refresh every n source updates */
     int32_t block_order;         /* 0: S[AC], 1: Gauss-Seidel SAC, 2: Jacobi [SAC] (below) */
-    int32_t reserved[4];
+    int32_t cal_model;           /* 0: r = 0 offsets per interval; 1: full geometric model (below) */
+    int32_t n_gate;              /* cal_model 1: gates g = 0 .. n_gate-1 (1..AGIS_MAX_GATE)   */
+    int32_t cal_j_per_k;         /* cal_model 1: short calibration intervals per long one      */
+    int32_t cal_col_bin;         /* cal_model 1: AC pixel columns per small-scale parameter    */
 } agis_config;
+
+/* Full geometric calibration (cal_model = 1; Sect. 3.4, Eq. etazeta; Sect. 5.3).  The
+ * observation lines of field f, CCD n, gate g, at AC pixel coordinate mu and time t in short
+ * interval j (the calibration intervals of the geometry) and long interval k = j / j_per_k:
+ *   AL  eta0_n + sum_r Deta_{r f n g j} L*_r(x) + deta_{n g k b}
+ *   AC  zeta0_fn(mu) + sum_r Dzeta_{r f n g k} L*_r(x)
+ * r = 0, 1, 2, x = (mu - 13.5) / AGIS_N_COL, L*_r the shifted Legendre polynomials, b the bin
+ * (of cal_col_bin columns) of the nearest column m = floor(mu + 1/2) - 14 (clamped to
+ * 0 .. AGIS_N_COL-1).  AL observations carry mu too (the AC pixel coordinate of the image).
+ * Parameter layout: groups (n, g, k) in the order n, g, k; AL group of 6 j_per_k + n_bin values
+ * (Deta[j within k][f][r], then deta[b]), then all AC groups of 6 values (Dzeta[f][r]);
+ * n_bin = ceil(AGIS_N_COL / cal_col_bin), n_k = ceil(n_cal_days / j_per_k),
+ * n_cal = 62 n_gate n_k (6 j_per_k + n_bin + 6).
+ * The C block solves each AL group's normals (Eq. normC) as the least-squares solution under
+ * Eq. cc2 (every gate), by eliminating each short interval's 6x6 block of large-scale terms
+ * onto the small-scale terms, imposing cc2 on that reduced system (null-space method) and
+ * back-substituting; each AC group's 6x6 normals by Algorithms C.1-C.3; then Eqs. cc1 and cc3
+ * by the projection of Eq. calCon.  Parameters without observations are held and counted as
+ * rank defects.  FP64 form only (precision 0). */
 
 /* Block order within an iteration (Sect. 4.6).  0, S[AC] (Eq. precondS(CAG)): A and C both
  * from the residuals after the source update, R = h - A d.  1, SAC (block Gauss-Seidel, Eq.
@@ -109,7 +133,8 @@ typedef struct agis_obs {
     const uint8_t* fov;          /* 0: preceding field (f = +1), 1: following (f = -1)   */
     const uint8_t* kind;         /* 0: AL (observed t), 1: AC (observed mu)              */
     const float* sigma;          /* formal standard uncertainty (rad)                    */
-    const double* mu;            /* AC pixel coordinate (AC observations; AL ignored)    */
+    const double* mu;            /* AC pixel coordinate (AC; AL too with cal_model 1)    */
+    const uint8_t* gate;         /* gate 0..n_gate-1 (cal_model 1), or NULL: all 0       */
 } agis_obs;
 
 /* Statistics of one block call. */
@@ -152,7 +177,8 @@ void agis_default_config(agis_config* cfg);
  *   src_ref    n_src x 4 reference (alpha, delta, mu_a*, mu_d) at t_ep in the ICRS for the
  *              frame rotator (subset S_PM of Sect. 6.1.4), or NULL (frame rotator disabled)
  *   att0       n_coef x 4 starting spline coefficients
- *   cal0       n_cal starting calibration offsets; n_cal = n_cal_days * 2 * (62 + 7):
+ *   cal0       n_cal starting calibration parameters; with cal_model 1 the layout above,
+ *              otherwise n_cal = n_cal_days * 2 * (62 + 7):
  *              AL offset of (interval d, field f, CCD n) at (d*2 + f)*62 + n,
  *              AC offset of (d, f, row r) at n_cal_days*124 + (d*2 + f)*7 + r
  *   stream     cudaStream_t to run on (NULL: the legacy default stream)
@@ -368,6 +394,39 @@ int agis_set_attnoise(agis_ctx* ctx, int64_t bucket_ns);
  * device memory, 3 x n_buckets FP64, caller-owned).  Synchronous.  Errors: AGIS_E_INVALID
  * (null ctx or n_buckets), AGIS_E_CUDA. */
 int agis_get_attnoise(agis_ctx* ctx, double* eps2_a, int32_t* n_buckets);
+
+/* ---------------------------------------------------------------------------------------
+ * Source partitions (Sects. 4.6, 7.1): several contexts, each holding the observations of one
+ * part of the sources (sorted, indices 0 .. n_src-1 of its own) and the whole attitude and
+ * calibration, iterate one problem.  The source update is local.  The attitude and
+ * calibration normals are sums over observations (Eqs. normAmod, normC), and the frame
+ * rotator's over sources (Eq. cond-mu3): each context accumulates its part, the caller adds
+ * the parts over the contexts (an all-reduce: the paper's accumulation of the DataTrain's
+ * normals on the servers, Sect. 7.1) and gives the sums back, and every context solves the
+ * same sums, so that all hold the same attitude and calibration.  One iteration:
+ *   agis_source_update;
+ *   for X in (AGIS_X_ATTITUDE, AGIS_X_CALIBRATION): agis_accumulate(X), agis_get_exchange(X),
+ *       sum over the contexts, agis_set_exchange(X), agis_solve_exchange(X);
+ *   the same with AGIS_X_FRAME (its sums are over the context's sources and need no source
+ *       update; it applies the rotation to the local sources and to the attitude).
+ * With one context this is agis_iterate's S[AC] iteration (the sums of one part are the sums).
+ *   AGIS_X_ATTITUDE     per knot interval, the 136 upper entries of the 16x16 normals of its four
+ *                       coefficients and the 16 right-hand sides (n_coef - 3) x 152 doubles
+ *   AGIS_X_CALIBRATION  per calibration parameter, sum W and -sum W R (n_cal x 2)
+ *   AGIS_X_FRAME        the 21 upper entries of the 6x6 normals and the 6 right-hand sides (27)
+ * Buffers are caller-owned (host or device).  FP64 form; the calibration exchange needs the
+ * offsets model (cal_model 0).  agis_accumulate synchronises; agis_solve_exchange returns the
+ * rank defects in out (and the applied (eps, omega) for the frame, if eps_omega_out is not
+ * NULL).  Errors: AGIS_E_INVALID (unknown buffer, call order, the restrictions above),
+ * AGIS_E_OOM, AGIS_E_CUDA. */
+#define AGIS_X_ATTITUDE 0
+#define AGIS_X_CALIBRATION 1
+#define AGIS_X_FRAME 2
+int agis_exchange_size(const agis_ctx* ctx, int32_t which, int64_t* n_doubles);
+int agis_accumulate(agis_ctx* ctx, int32_t which);
+int agis_get_exchange(agis_ctx* ctx, int32_t which, double* out);
+int agis_set_exchange(agis_ctx* ctx, int32_t which, const double* in);
+int agis_solve_exchange(agis_ctx* ctx, int32_t which, agis_block_stats* out, double eps_omega_out[6]);
 
 /* ---------------------------------------------------------------------------------------
  * Launch-shape autotuner (iteration control)

@@ -19,7 +19,7 @@ ERRORS = {-1: "AGIS_E_INVALID", -2: "AGIS_E_CUDA", -3: "AGIS_E_OOM", -4: "AGIS_E
 N_CCD, N_ROW = 62, 7
 
 # every symbol declared in include/agis.h
-ABI_VERSION = 7  # AGIS_ABI_VERSION of include/agis.h
+ABI_VERSION = 8  # AGIS_ABI_VERSION of include/agis.h
 EXPORTS = (
     "agis_default_config", "agis_init", "agis_source_update", "agis_attitude_update", "agis_calibration_update",
     "agis_frame_rotate", "agis_iterate", "agis_evaluate", "agis_get_sources", "agis_get_attitude",
@@ -28,8 +28,10 @@ EXPORTS = (
     "agis_abi_version", "agis_source_update_static", "agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad",
     "agis_mlp_adam", "agis_proposal_targets", "agis_set_proposal", "agis_get_proposal_features",
     "agis_copy_sources_device", "agis_set_asi", "agis_asi_estimate", "agis_autotune", "agis_get_tuning",
-    "agis_set_tuning", "agis_set_attnoise", "agis_get_attnoise",
+    "agis_set_tuning", "agis_set_attnoise", "agis_get_attnoise", "agis_exchange_size", "agis_accumulate",
+    "agis_get_exchange", "agis_set_exchange", "agis_solve_exchange",
 )
+X_ATTITUDE, X_CALIBRATION, X_FRAME = 0, 1, 2  # AGIS_X_* of include/agis.h
 KNOBS = ("obs_pass", "src_batch", "mix_sums", "mix_solve5", "att_accum", "cal_accum")  # AGIS_KNOB_* order
 STATIC_MAX_OBS = 16384
 MLP_N_IN, MLP_N_OUT, MLP_N_PARAMS, MLP_PACKED_BYTES = 22, 5, 5957, 16032
@@ -53,13 +55,13 @@ class Config(C.Structure):
         ("seg_overlap", C.c_int32), ("frame_each_iter", C.c_int32), ("block_mask", C.c_int32),
         ("use_graph", C.c_int32), ("pivot_tol", C.c_double), ("max_obs_per_source", C.c_int32),
         ("precision", C.c_int32), ("refresh_every", C.c_int32), ("block_order", C.c_int32),
-        ("reserved", C.c_int32 * 4),
+        ("cal_model", C.c_int32), ("n_gate", C.c_int32), ("cal_j_per_k", C.c_int32), ("cal_col_bin", C.c_int32),
     ]
 
 
 class Obs(C.Structure):
     _fields_ = [("t_ns", C.c_void_p), ("src", C.c_void_p), ("ccd", C.c_void_p), ("fov", C.c_void_p),
-                ("kind", C.c_void_p), ("sigma", C.c_void_p), ("mu", C.c_void_p)]
+                ("kind", C.c_void_p), ("sigma", C.c_void_p), ("mu", C.c_void_p), ("gate", C.c_void_p)]
 
 
 class BlockStats(C.Structure):
@@ -142,6 +144,15 @@ def load():
         lib.agis_set_tuning.argtypes = [V, P, C.c_int32]
         lib.agis_set_attnoise.argtypes = [V, C.c_int64]
         lib.agis_get_attnoise.argtypes = [V, P, C.POINTER(C.c_int32)]
+        lib.agis_exchange_size.argtypes = [V, C.c_int32, C.POINTER(C.c_int64)]
+        lib.agis_exchange_size.restype = I
+        lib.agis_accumulate.argtypes = [V, C.c_int32]
+        lib.agis_accumulate.restype = I
+        for f in ("agis_get_exchange", "agis_set_exchange"):
+            getattr(lib, f).argtypes = [V, C.c_int32, P]
+            getattr(lib, f).restype = I
+        lib.agis_solve_exchange.argtypes = [V, C.c_int32, C.POINTER(BlockStats), P]
+        lib.agis_solve_exchange.restype = I
         for f in ("agis_mlp_pack", "agis_mlp_forward", "agis_mlp_loss_grad", "agis_mlp_adam", "agis_proposal_targets",
                   "agis_set_proposal", "agis_get_proposal_features", "agis_copy_sources_device", "agis_set_asi",
                   "agis_asi_estimate", "agis_autotune", "agis_get_tuning", "agis_set_tuning", "agis_set_attnoise",
@@ -199,7 +210,7 @@ class Agis:
         lib = load()
         self._lib = lib
         self._keep = (obs, src0, att0, cal0, src_ref)
-        o = Obs(*(_ptr(obs[k]) for k in ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu")))
+        o = Obs(*(_ptr(obs.get(k)) for k in ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu", "gate")))
         self.n_obs = int(obs["t_ns"].shape[0])
         self.n_src = int(src0.shape[0])
         self.n_coef = int(att0.shape[0])
@@ -364,6 +375,34 @@ class Agis:
         self._check(self._lib.agis_get_attnoise(self.ctx, out.ctypes.data, C.byref(nb)))
         return out
 
+    # source partitions: local sums, exchange, solve from the summed parts
+    def exchange_size(self, which):
+        n = C.c_int64(0)
+        self._check(self._lib.agis_exchange_size(self.ctx, int(which), C.byref(n)))
+        return n.value
+
+    def accumulate(self, which):
+        self._check(self._lib.agis_accumulate(self.ctx, int(which)))
+
+    def get_exchange(self, which, out=None):
+        """The context's partial sums into out (NumPy array or torch tensor, host or device)."""
+        if out is None:
+            out = np.empty(self.exchange_size(which), dtype=np.float64)
+        self._check(self._lib.agis_get_exchange(self.ctx, int(which), _ptr(out)))
+        return out
+
+    def set_exchange(self, which, buf):
+        self._check(self._lib.agis_set_exchange(self.ctx, int(which), _ptr(buf)))
+
+    def solve_exchange(self, which):
+        st = BlockStats()
+        eo = np.zeros(6)
+        self._check(self._lib.agis_solve_exchange(self.ctx, int(which), C.byref(st), eo.ctypes.data))
+        d = st.as_dict()
+        if which == X_FRAME:
+            d["frame"] = eo
+        return d
+
 
 def _mlp_call(name, *args):
     lib = load()
@@ -414,18 +453,29 @@ def asi_estimate(d_prev, d_cur, stride, lambda_max, scratch, est, stream=None):
 
 
 def obs_from_dataset(ds, device=None):
-    """Observation arrays of a synth.Dataset, on the host or copied to a torch device."""
+    """Observation arrays of a synth.Dataset, on the host or copied to a torch device (the gates
+    with the full calibration model only)."""
     arrs = dict(t_ns=ds.t_ns, src=ds.src, ccd=ds.ccd, fov=ds.fov, kind=ds.kind, sigma=ds.sigma, mu=ds.mu)
+    if ds.geometry.get("cal_generic"):
+        arrs["gate"] = ds.gate
     if device is None:
         return {k: np.ascontiguousarray(v) for k, v in arrs.items()}
     import torch
     return {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in arrs.items()}
 
 
+def calibration_config(geometry: dict) -> dict:
+    """The agis_config fields of a dataset's calibration model."""
+    if not geometry.get("cal_generic"):
+        return dict(cal_model=0)
+    return dict(cal_model=1, n_gate=int(geometry["n_gate"]), cal_j_per_k=int(geometry["cal_j_per_k"]),
+                cal_col_bin=int(geometry["cal_col_bin"]))
+
+
 def from_dataset(ds, cfg=None, device=None, with_ref=True, stream=None, **cfg_over):
     """Create a context from a synth.Dataset (starting values, truth as frame reference)."""
     if cfg is None:
-        cfg = default_config(**cfg_over)
+        cfg = default_config(**{**calibration_config(ds.geometry), **cfg_over})
     ref = np.ascontiguousarray(ds.src_true[:, [0, 1, 3, 4]]) if with_ref else None
     return Agis(ds.geometry, cfg, obs_from_dataset(ds, device), np.ascontiguousarray(ds.src0),
                 np.ascontiguousarray(ds.att0), np.ascontiguousarray(ds.cal0), src_ref=ref, stream=stream)
@@ -435,7 +485,7 @@ def source_update_static(geometry: dict, cfg: Config, obs: dict, src, att, cal, 
                          stats_out=None, max_obs_per_source=STATIC_MAX_OBS, stream=None):
     """agis_source_update_static on device arrays (torch CUDA tensors); src is updated in place."""
     lib = load()
-    o = Obs(*(_ptr(obs[k]) for k in ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu")))
+    o = Obs(*(_ptr(obs.get(k)) for k in ("t_ns", "src", "ccd", "fov", "kind", "sigma", "mu", "gate")))
     G = geometry_from_dict(geometry)
     s = C.c_void_p(stream) if stream is not None else None
     rc = lib.agis_source_update_static(C.byref(G), C.byref(cfg), C.byref(o), int(obs["t_ns"].shape[0]), _ptr(src),

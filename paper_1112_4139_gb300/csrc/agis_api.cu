@@ -55,6 +55,17 @@ void launch_prop_rec(int32_t n_src, const int64_t* src_off, const double* scratc
                      cudaStream_t s);
 void launch_asi(int32_t n_src, int32_t stride, const double* hist, double lam_max, unsigned long long* keys,
                 double* est, const double* d, double* src, double* corr, cudaStream_t s);
+void launch_calgen(const DevGeo& G, int64_t n_groups, const ObsRec* rec, const double* mu, const CalGenWork& w,
+                   double tol, double* cal, cudaStream_t s);
+int calgen_prepare();
+void launch_cal_sums(int n_cal, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double* sums,
+                     const Shapes& sh, cudaStream_t s);
+void launch_cal_from_sums(int n_cal, int n_days, const double* sums, double tol, double* dtil, int* rd, double* cal,
+                          cudaStream_t s);
+void launch_frame_sums(int n, const int32_t* subset, const double* src, const double* ref, const DevGeo& G,
+                       double* partial, int n_part, double* sums, cudaStream_t s);
+void launch_frame_from_sums(const DevGeo& G, int n_src, double* src, double* att, const double* sums, double tol,
+                            double* eo, cudaStream_t s);
 void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double tol,
                 double* dtil, int* rd, double* cal, const Shapes& sh, cudaStream_t s);
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,
@@ -77,12 +88,13 @@ using namespace agis;
 // -----------------------------------------------------------------------------------------
 namespace {
 
+// gate: per observation (full calibration model, n_gate > 0) or NULL
 __global__ void k_validate_pack(int64_t n, const int64_t* __restrict__ t, const int32_t* __restrict__ src,
                                 const uint8_t* __restrict__ ccd, const uint8_t* __restrict__ fov,
                                 const uint8_t* __restrict__ kind, const float* __restrict__ sigma,
                                 const double* __restrict__ mu, int32_t n_src, int64_t cal_t0, int64_t cal_dt,
-                                int32_t n_days, const int32_t* __restrict__ ccd_row, uint32_t* __restrict__ meta,
-                                int* __restrict__ err) {
+                                int32_t n_days, const int32_t* __restrict__ ccd_row, const uint8_t* __restrict__ gate,
+                                int n_gate, uint32_t* __restrict__ meta, int* __restrict__ err) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = src[o];
         const int c = ccd[o], f = fov[o], k = kind[o];
@@ -92,8 +104,14 @@ __global__ void k_validate_pack(int64_t n, const int64_t* __restrict__ t, const 
         if (o > 0 && src[o - 1] > s) bad |= 2;
         if (c >= AGIS_N_CCD || f > 1 || k > 1) bad |= 4;
         if (!(sg > 0.0f) || !isfinite(sg)) bad |= 8;
-        if (k == 1 && !isfinite(mu[o])) bad |= 16;
+        if ((k == 1 || n_gate > 0) && !isfinite(mu[o])) bad |= 16;
+        const int gt = gate ? gate[o] : 0;
+        if (n_gate > 0 && gt >= n_gate) bad |= 64;
         if (bad) atomicOr(err, bad);
+        if (n_gate > 0) {
+            meta[o] = (uint32_t)(c & 63) | ((uint32_t)f << 6) | ((uint32_t)k << 7) | ((uint32_t)gt << 8);
+            continue;
+        }
         const int64_t rel = t[o] - cal_t0;
         int64_t day = rel < 0 ? 0 : rel / cal_dt;
         if (day > n_days - 1) day = n_days - 1;
@@ -119,9 +137,38 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, const T* 
         out[o] = in[perm[o]];
 }
 __global__ void k_gather_mu(int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ meta,
-                            const double* __restrict__ in, double* __restrict__ out) {
+                            const double* __restrict__ in, double* __restrict__ out, int all) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
-        out[o] = meta_kind(meta[o]) ? in[perm[o]] : 0.0;
+        out[o] = (all || meta_kind(meta[o])) ? in[perm[o]] : 0.0;
+}
+
+// full calibration model: C-block order keys, AL observations by (cell, bin) with the cell
+// (n, g, j) = group * j_per_k + j within k, then AC observations by group
+__global__ void k_calgen_keys(DevGeo G, int64_t n, const int64_t* __restrict__ t, const uint32_t* __restrict__ meta,
+                              const double* __restrict__ mu, int64_t n_cells, int32_t* __restrict__ key,
+                              uint32_t* __restrict__ val) {
+    const CalGen& C = G.cg;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = meta[o];
+        const CalPos p = cal_position(C, t[o], m, mu[o]);
+        key[o] = meta_kind(m) == 0 ? (int32_t)((p.grp * C.j_per_k + p.jj) * C.n_bin + p.bin)
+                                   : (int32_t)(n_cells * C.n_bin + p.grp);
+        val[o] = (uint32_t)o;
+    }
+}
+// offsets of the AL cells (key c * n_bin) and of the AC groups (key n_cells * n_bin + g)
+__global__ void k_calgen_off(const int32_t* __restrict__ keys, int64_t n, int64_t n_cells, int64_t n_groups, int nb,
+                             int64_t* __restrict__ out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n_cells + n_groups;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = v <= n_cells ? v * nb : n_cells * nb + (v - n_cells);
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)keys[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        out[v] = lo;
+    }
 }
 
 // out[perm[o]] = in[o]: internal order back to the caller's order
@@ -269,11 +316,19 @@ struct agis_ctx {
     double *bandc = nullptr, *rhs = nullptr, *urow = nullptr, *yv = nullptr, *xs = nullptr;
     int* seg_rd = nullptr;
     long long* isum = nullptr;    // [0] A rank defect, [1] C rank defect
-    // C block
+    // C block (full calibration model: its own order, offsets and work arrays)
+    bool cal_generic = false;
+    int64_t cg_groups = 0;
+    CalGenWork cgw{};
     uint32_t* perm_c = nullptr;
     int64_t* cal_off = nullptr;
     double* dtil = nullptr;
     int* cal_rd = nullptr;
+    // exchange buffers of a source partition: calibration sums (2 per parameter), frame sums
+    // (27); the attitude's are the interval blocks blk
+    double* xcal = nullptr;
+    double* xframe = nullptr;
+    bool x_att_ready = false, x_cal_ready = false, x_frame_ready = false;
     // frame rotator
     double* fpart = nullptr;
     int n_fpart = 0;
@@ -289,8 +344,10 @@ struct agis_ctx {
     bool have_s = false;
     bool have_s_out = false;    // the S block's hand-over (R, W) exists and no state was set since
     bool a_since_c = false;     // an A update not yet seen by a C update (block Gauss-Seidel)
-    static constexpr int kEvents = 14;
+    // events 0-13 on the stream; 14, 15 the C block's start and end on the second stream
+    static constexpr int kEvents = 16;
     cudaEvent_t ev[kEvents];
+    cudaStream_t stream_c = nullptr;   // the C block beside the A block (S[AC] and [SAC] orders)
     double ktimes[5] = {0, 0, 0, 0, 0};
     // per-block graphs: 0 S observation pass (FP64 model, or the mixed form's linearized
     // correction), 1 A, 2 C, 3 frame, 4 mixed S pass with the full FP64 model, 5 S solves,
@@ -539,6 +596,11 @@ void enqueue_c(agis_ctx* c, bool with_att = true) {
         else
             launch_rec_att_correct(c->G, c->n_obs, c->rec, c->datt64, c->stream);
     }
+    if (c->cal_generic) {
+        launch_calgen(c->G, c->cg_groups, c->rec, c->mu, c->cgw, c->st.pivot_tol, c->cal, c->stream);
+        launch_int_sum((int)(c->cg_groups * (c->G.cg.j_per_k + 2)), c->cgw.rd, c->isum + 1, c->stream);
+        return;
+    }
     if (c->mixed)
         launch_mix_cal(c->n_cal, c->n_days, c->perm_c, c->cal_off, c->mo, c->dtil, c->cal_rd, c->cal, c->d_cal,
                        c->sh, c->stream);
@@ -667,6 +729,7 @@ void agis_destroy(agis_ctx* c) {
     if (c->hstat) cudaFreeHost(c->hstat);
     if (c->hisum) cudaFreeHost(c->hisum);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->stream_c) cudaStreamDestroy(c->stream_c);
     for (int i = 0; i < agis_ctx::kEvents; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;
@@ -688,8 +751,35 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     if (n_obs < 0 || n_src < 0) return bail(fail(c, AGIS_E_INVALID, "negative size"));
     if (n_obs >= ((int64_t)1 << 32)) return bail(fail(c, AGIS_E_INVALID, "more than 2^32-1 observations"));
     if (n_coef < 4 || n_coef != geo->n_coef) return bail(fail(c, AGIS_E_INVALID, "n_coef < 4 or != geo->n_coef"));
-    if (geo->n_cal_days < 1 || n_cal != geo->n_cal_days * 2 * (AGIS_N_CCD + AGIS_N_ROW))
+    if (cfg->cal_model != 0 && cfg->cal_model != 1) return bail(fail(c, AGIS_E_INVALID, "cal_model must be 0 or 1"));
+    CalGen cg{};
+    if (cfg->cal_model == 1) {
+        if (cfg->n_gate < 1 || cfg->n_gate > AGIS_MAX_GATE || cfg->cal_j_per_k < 1 || cfg->cal_col_bin < 1 ||
+            cfg->cal_col_bin > AGIS_N_COL || geo->n_cal_days < 1)
+            return bail(fail(c, AGIS_E_INVALID, "full calibration: n_gate 1..AGIS_MAX_GATE, cal_j_per_k >= 1, "
+                                                "cal_col_bin 1..AGIS_N_COL"));
+        if (cfg->precision != 0)
+            return bail(fail(c, AGIS_E_INVALID, "the full calibration model needs the FP64 form (precision 0)"));
+        cg.on = 1;
+        cg.n_gate = cfg->n_gate;
+        cg.j_per_k = cfg->cal_j_per_k;
+        cg.col_bin = cfg->cal_col_bin;
+        cg.n_bin = (AGIS_N_COL + cfg->cal_col_bin - 1) / cfg->cal_col_bin;
+        cg.n_j = geo->n_cal_days;
+        cg.n_k = (geo->n_cal_days + cfg->cal_j_per_k - 1) / cfg->cal_j_per_k;
+        cg.al_size = 6 * cg.j_per_k + cg.n_bin;
+        const int64_t n_groups = (int64_t)AGIS_N_CCD * cg.n_gate * cg.n_k;
+        cg.n_al = n_groups * cg.al_size;
+        cg.t0 = geo->cal_t0_ns;
+        cg.dt = geo->cal_dt_ns;
+        cg.inv_ncol = 1.0 / (double)AGIS_N_COL;
+        if ((int64_t)n_cal != cg.n_al + 6 * n_groups)
+            return bail(fail(c, AGIS_E_INVALID, "n_cal != 62 n_gate n_k (6 j_per_k + n_bin + 6) (full calibration)"));
+        if ((n_groups * cg.j_per_k + 1) * cg.n_bin + n_groups >= ((int64_t)1 << 31))
+            return bail(fail(c, AGIS_E_INVALID, "full calibration layout too large for the C-block order keys"));
+    } else if (geo->n_cal_days < 1 || n_cal != geo->n_cal_days * 2 * (AGIS_N_CCD + AGIS_N_ROW)) {
         return bail(fail(c, AGIS_E_INVALID, "n_cal != n_cal_days * 138"));
+    }
     if (geo->knot_dt_ns <= 0 || geo->cal_dt_ns <= 0 || !(geo->year_s > 0) || !(geo->focal_length > 0))
         return bail(fail(c, AGIS_E_INVALID, "non-positive interval, year or focal length"));
     if (n_obs > 0 && (!obs->t_ns || !obs->src || !obs->ccd || !obs->fov || !obs->kind || !obs->sigma || !obs->mu))
@@ -721,6 +811,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     // device geometry
     DevGeo& G = c->G;
     fill_devgeo(geo, n_coef, G);
+    G.cg = cg;
+    c->cal_generic = cg.on != 0;
     Settings& st = c->st;
     st.robust = cfg->robust;
     st.n_rounds = cfg->n_rounds;
@@ -731,6 +823,8 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     st.pivot_tol = cfg->pivot_tol;
     st.handover_h = cfg->block_order == 2 ? 1 : 0;
     for (int i = 0; i < agis_ctx::kEvents; i++) cudaEventCreate(&c->ev[i]);
+    if (cudaStreamCreateWithFlags(&c->stream_c, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(c, AGIS_E_CUDA, "cudaStreamCreate (C block)"));
     if (cudaMallocHost(&c->hstat, 32 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->hisum, 4 * sizeof(long long)) != cudaSuccess)
         return bail(fail(c, AGIS_E_OOM, "pinned host buffer"));
@@ -739,7 +833,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     int* derr = nullptr;
     int32_t* d_ccdrow = nullptr;
     int rc = AGIS_OK;
-    TmpDev tb_t, tb_src, tb_sig, tb_mu, tb_8, tb_meta;
+    TmpDev tb_t, tb_src, tb_sig, tb_mu, tb_8, tb_meta, tb_gate;
+    uint8_t* gate_in = nullptr;
+    if (c->cal_generic && obs->gate && n > 0 && (rc = tb_gate.alloc(c, &gate_in, n))) return bail(rc);
     int64_t* t_in = nullptr;
     int32_t* src_in = nullptr;
     float* sig_in = nullptr;
@@ -762,13 +858,15 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         CP(tmp8 + 2 * n, obs->kind, n);
         CP(sig_in, obs->sigma, n * sizeof(float));
         CP(mu_in, obs->mu, n * sizeof(double));
+        if (gate_in) CP(gate_in, obs->gate, n);
     }
     CP(d_ccdrow, geo->ccd_row, AGIS_N_CCD * sizeof(int32_t));
     cudaMemsetAsync(derr, 0, sizeof(int), s);
     if (n > 0) {
         k_validate_pack<<<grid_for(n, 256), 256, 0, s>>>(n, t_in, src_in, tmp8, tmp8 + n, tmp8 + 2 * n, sig_in, mu_in,
                                                          n_src, geo->cal_t0_ns, geo->cal_dt_ns, geo->n_cal_days,
-                                                         d_ccdrow, meta_in, derr);
+                                                         d_ccdrow, gate_in, c->cal_generic ? cg.n_gate : 0, meta_in,
+                                                         derr);
     }
     // ---- state
     if ((rc = dalloc(c, &c->src, 5 * (size_t)n_src)) || (rc = dalloc(c, &c->att, 4 * (size_t)n_coef)) ||
@@ -789,12 +887,12 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         cuda_check(c, cudaStreamSynchronize(s), "validate (sync)"))
         return bail(AGIS_E_CUDA);
     if (herr) {
-        static const char* what[6] = {"source index out of range", "observations not sorted by source",
+        static const char* what[7] = {"source index out of range", "observations not sorted by source",
                                       "ccd, fov or kind out of range", "sigma not positive and finite",
-                                      "mu of an AC observation not finite",
-                                      "non-finite starting value (src0, att0 or cal0)"};
+                                      "mu of an AC observation (or of any, full calibration) not finite",
+                                      "non-finite starting value (src0, att0 or cal0)", "gate out of range"};
         std::string msg = "invalid input:";
-        for (int b = 0; b < 6; b++)
+        for (int b = 0; b < 7; b++)
             if (herr & (1 << b)) msg += std::string(" ") + what[b] + ";";
         return bail(fail(c, AGIS_E_INVALID, msg));
     }
@@ -829,7 +927,7 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
     if ((rc = dalloc(c, &c->meta, n))) return bail(rc);
     k_gather<uint32_t><<<grid_for(n, 256), 256, 0, s>>>(n, pin, meta_in, c->meta);
     if ((rc = dalloc(c, &c->mu, n))) return bail(rc);
-    k_gather_mu<<<grid_for(n, 256), 256, 0, s>>>(n, pin, c->meta, mu_in, c->mu);
+    k_gather_mu<<<grid_for(n, 256), 256, 0, s>>>(n, pin, c->meta, mu_in, c->mu, c->cal_generic ? 1 : 0);
     if (cuda_check(c, cudaStreamSynchronize(s), "reorder")) return bail(AGIS_E_CUDA);
     tb_mu.release();
     tb_meta.release();
@@ -880,12 +978,51 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         }
         k_lower_bound<int32_t><<<grid_for(c->n_iv + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)c->n_iv + 1, c->ivl_off);
         // calibration order
-        if ((rc = dalloc(c, &c->perm_c, n)) || (rc = dalloc(c, &c->cal_off, (size_t)n_cal + 1))) return bail(rc);
-        if (n > 0) {
-            k_cal_keys<<<grid_for(n, 256), 256, 0, s>>>(n, c->meta, k_in, v_in);
-            if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_c, n, bits_for(n_cal)))) return bail(rc);
+        if (c->cal_generic) {
+            const int64_t ng = (int64_t)AGIS_N_CCD * cg.n_gate * cg.n_k, ncell = ng * cg.j_per_k;
+            const int nb = cg.n_bin;
+            c->cg_groups = ng;
+            CalGenWork& w = c->cgw;
+            uint32_t* perm = nullptr;
+            int64_t* off = nullptr;
+            double* cc2 = nullptr;
+            if ((rc = dalloc(c, &perm, n)) || (rc = dalloc(c, &off, (size_t)(ncell + ng + 1))) ||
+                (rc = dalloc(c, &w.V, (size_t)ncell * 6 * nb)) || (rc = dalloc(c, &w.E, (size_t)ncell * nb)) ||
+                (rc = dalloc(c, &w.bs, (size_t)ncell * nb)) || (rc = dalloc(c, &w.cw, (size_t)ncell * 18)) ||
+                (rc = dalloc(c, &w.S, (size_t)ng * nb * nb)) || (rc = dalloc(c, &w.r, (size_t)ng * nb)) ||
+                (rc = dalloc(c, &w.Et, (size_t)ng * nb)) || (rc = dalloc(c, &w.H, (size_t)ng * 3 * nb)) ||
+                (rc = dalloc(c, &w.v, (size_t)ng * nb)) || (rc = dalloc(c, &w.idx, (size_t)ng * nb)) ||
+                (rc = dalloc(c, &cc2, 3 * (size_t)nb)) || (rc = dalloc(c, &w.d, (size_t)n_cal)) ||
+                (rc = dalloc(c, &w.rd, (size_t)(ncell + 2 * ng))))
+                return bail(rc);
+            // cc2 weights: sum of L*_r((m + 14 - 13.5) / n_col) over the columns m of each bin
+            std::vector<double> hw(3 * (size_t)nb, 0.0);
+            for (int m = 0; m < AGIS_N_COL; m++) {
+                const double x = (m + 0.5) / (double)AGIS_N_COL;
+                const int b = m / cg.col_bin;
+                hw[b] += 1.0;
+                hw[(size_t)nb + b] += 2.0 * x - 1.0;
+                hw[2 * (size_t)nb + b] += 6.0 * x * x - 6.0 * x + 1.0;
+            }
+            CP(cc2, hw.data(), hw.size() * sizeof(double));
+            if (cuda_check(c, cudaMemsetAsync(w.d, 0, (size_t)n_cal * 8, s), "calibration work")) return bail(AGIS_E_CUDA);
+            if (n > 0) {
+                k_calgen_keys<<<grid_for(n, 256), 256, 0, s>>>(G, n, c->t_ns, c->meta, c->mu, ncell, k_in, v_in);
+                if ((rc = sort_pairs(c, k_in, k_out, v_in, perm, n, bits_for((ncell + 1) * nb + ng)))) return bail(rc);
+            }
+            k_calgen_off<<<grid_for(ncell + ng + 1, 256), 256, 0, s>>>(k_out, n, ncell, ng, nb, off);
+            w.perm = perm;
+            w.off = off;
+            w.cc2w = cc2;
+            if (calgen_prepare() != 0) return bail(fail(c, AGIS_E_CUDA, "shared-memory attribute (calibration)"));
+        } else {
+            if ((rc = dalloc(c, &c->perm_c, n)) || (rc = dalloc(c, &c->cal_off, (size_t)n_cal + 1))) return bail(rc);
+            if (n > 0) {
+                k_cal_keys<<<grid_for(n, 256), 256, 0, s>>>(n, c->meta, k_in, v_in);
+                if ((rc = sort_pairs(c, k_in, k_out, v_in, c->perm_c, n, bits_for(n_cal)))) return bail(rc);
+            }
+            k_lower_bound<int32_t><<<grid_for(n_cal + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)n_cal + 1, c->cal_off);
         }
-        k_lower_bound<int32_t><<<grid_for(n_cal + 1, 256), 256, 0, s>>>(k_out, n, (int64_t)n_cal + 1, c->cal_off);
         if (cuda_check(c, cudaStreamSynchronize(s), "orders")) return bail(AGIS_E_CUDA);
     }
     c->n_sblocks = c->n_sm * 8;
@@ -1164,9 +1301,20 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
                     "stats");
         }
         AGIS_CU(c, cudaEventRecord(c->ev[9], c->stream), "event");
+        // S[AC] and [SAC]: A and C read the same hand-over and write disjoint state, so the C
+        // graph runs on a second stream beside the A graph (Sect. 4.6: A and C are independent
+        // given S); block Gauss-Seidel SAC keeps C after A
+        const bool c_beside = graph && (mask & 2) && (mask & 4) && c->cfg.block_order != 1;
+        if (c_beside) {
+            AGIS_CU(c, cudaStreamWaitEvent(c->stream_c, c->ev[9], 0), "fork");
+            AGIS_CU(c, cudaEventRecord(c->ev[14], c->stream_c), "event");
+            AGIS_CU(c, cudaGraphLaunch(c->graph_execs[2], c->stream_c), "graph launch");
+            AGIS_CU(c, cudaEventRecord(c->ev[15], c->stream_c), "event");
+        }
         if (mask & 2) AGIS_TRY(run_block(1));
         AGIS_CU(c, cudaEventRecord(c->ev[10], c->stream), "event");
-        if (mask & 4) AGIS_TRY(run_block(2));
+        if (c_beside) AGIS_CU(c, cudaStreamWaitEvent(c->stream, c->ev[15], 0), "join");
+        else if (mask & 4) AGIS_TRY(run_block(2));
         if (do_frame) AGIS_TRY(run_block(3));
         AGIS_CU(c, cudaEventRecord(c->ev[11], c->stream), "event");
         c->since_prop++;
@@ -1193,7 +1341,7 @@ int agis_iterate(agis_ctx* c, int32_t n_iter, agis_iter_stats* per_iter, int32_t
             it.s.pass_ms = prop_state == 0 ? elapsed(c, 8, 12) : -1.0;
             it.s.full_eval = (mask & 1) && (!c->mixed || refresh) ? 1 : 0;
             it.a.elapsed_ms = elapsed(c, 9, 10);
-            it.c.elapsed_ms = elapsed(c, 10, 11);
+            it.c.elapsed_ms = c_beside ? elapsed(c, 14, 15) : elapsed(c, 10, 11);
             it.elapsed_ms = elapsed(c, 8, 11);
             it.proposal = prop_state;
             it.asi_factor = 1.0;
@@ -1581,6 +1729,127 @@ int agis_get_kernel_times(const agis_ctx* c, double* ms) {
 }
 
 }  // extern "C"
+
+// --- source partitions: local sums, exchange, solve from the reduced sums --------------------
+namespace {
+int x_size(const agis_ctx* c, int which, int64_t* n) {
+    switch (which) {
+        case AGIS_X_ATTITUDE: *n = (int64_t)c->n_iv * kBlkVals; return AGIS_OK;
+        case AGIS_X_CALIBRATION: *n = 2 * (int64_t)c->n_cal; return AGIS_OK;
+        case AGIS_X_FRAME: *n = 27; return AGIS_OK;
+        default: return AGIS_E_INVALID;
+    }
+}
+double* x_buf(agis_ctx* c, int which) {
+    return which == AGIS_X_ATTITUDE ? c->blk : which == AGIS_X_CALIBRATION ? c->xcal : c->xframe;
+}
+int x_check(agis_ctx* c, int which) {
+    if (c->mixed) return fail(c, AGIS_E_INVALID, "the exchange of partial sums needs the FP64 form (precision 0)");
+    if (which == AGIS_X_CALIBRATION && c->cal_generic)
+        return fail(c, AGIS_E_INVALID, "the exchange of calibration sums needs the offsets model (cal_model 0)");
+    if (which == AGIS_X_FRAME && !c->ref) return fail(c, AGIS_E_INVALID, "no frame-rotator reference");
+    int64_t n = 0;
+    if (x_size(c, which, &n) != AGIS_OK) return fail(c, AGIS_E_INVALID, "unknown exchange buffer");
+    return AGIS_OK;
+}
+}  // namespace
+
+int agis_exchange_size(const agis_ctx* c, int32_t which, int64_t* n_doubles) {
+    if (!c || !n_doubles) return AGIS_E_INVALID;
+    return x_size(c, which, n_doubles);
+}
+
+int agis_accumulate(agis_ctx* c, int32_t which) {
+    if (!c) return AGIS_E_INVALID;
+    AGIS_TRY(x_check(c, which));
+    if (which != AGIS_X_FRAME && !c->have_s)
+        return fail(c, AGIS_E_INVALID, "the attitude and calibration sums need a source update first");
+    if (which == AGIS_X_ATTITUDE) {
+        launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, c->rec,
+                         c->an.eps2 ? c->an_w : nullptr, c->att, c->blk, c->sh, c->stream);
+        c->x_att_ready = true;
+    } else if (which == AGIS_X_CALIBRATION) {
+        if (!c->xcal) AGIS_TRY(dalloc(c, &c->xcal, 2 * (size_t)c->n_cal));
+        // block Gauss-Seidel: the residuals C reads take the attitude update (once per A update)
+        if (c->cfg.block_order == 1 && c->a_since_c) {
+            launch_rec_att_correct(c->G, c->n_obs, c->rec, c->datt64, c->stream);
+            c->a_since_c = false;
+        }
+        launch_cal_sums(c->n_cal, c->perm_c, c->cal_off, c->rec, c->xcal, c->sh, c->stream);
+        c->x_cal_ready = true;
+    } else {
+        if (!c->xframe) AGIS_TRY(dalloc(c, &c->xframe, 27));
+        launch_frame_sums(c->n_src, nullptr, c->src, c->ref, c->G, c->fpart, c->n_fpart, c->xframe, c->stream);
+        c->x_frame_ready = true;
+    }
+    AGIS_CU(c, cudaGetLastError(), "accumulate");
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "accumulate (sync)");
+}
+
+int agis_get_exchange(agis_ctx* c, int32_t which, double* out) {
+    if (!c || !out) return AGIS_E_INVALID;
+    AGIS_TRY(x_check(c, which));
+    int64_t n = 0;
+    x_size(c, which, &n);
+    double* b = x_buf(c, which);
+    if (!b) return fail(c, AGIS_E_INVALID, "no sums accumulated yet");
+    AGIS_CU(c, cudaMemcpyAsync(out, b, (size_t)n * 8, cudaMemcpyDefault, c->stream), "get exchange");
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "get exchange (sync)");
+}
+
+int agis_set_exchange(agis_ctx* c, int32_t which, const double* in) {
+    if (!c || !in) return AGIS_E_INVALID;
+    AGIS_TRY(x_check(c, which));
+    int64_t n = 0;
+    x_size(c, which, &n);
+    if (which == AGIS_X_CALIBRATION && !c->xcal) AGIS_TRY(dalloc(c, &c->xcal, 2 * (size_t)c->n_cal));
+    if (which == AGIS_X_FRAME && !c->xframe) AGIS_TRY(dalloc(c, &c->xframe, 27));
+    AGIS_CU(c, cudaMemcpyAsync(x_buf(c, which), in, (size_t)n * 8, cudaMemcpyDefault, c->stream), "set exchange");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "set exchange (sync)");
+    if (which == AGIS_X_ATTITUDE) c->x_att_ready = true;
+    if (which == AGIS_X_CALIBRATION) c->x_cal_ready = true;
+    if (which == AGIS_X_FRAME) c->x_frame_ready = true;
+    return AGIS_OK;
+}
+
+int agis_solve_exchange(agis_ctx* c, int32_t which, agis_block_stats* out, double eps_omega_out[6]) {
+    if (!c) return AGIS_E_INVALID;
+    AGIS_TRY(x_check(c, which));
+    if (out) std::memset(out, 0, sizeof(*out));
+    record(c, 0);
+    if (which == AGIS_X_ATTITUDE) {
+        if (!c->x_att_ready) return fail(c, AGIS_E_INVALID, "no attitude sums accumulated or set");
+        launch_att_solve(c->n_seg, c->max_seg_knots, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u,
+                         c->blk, c->bandc, c->rhs, c->urow, c->yv, c->xs, c->st.pivot_tol, c->seg_rd, c->att, nullptr,
+                         c->datt64, c->stream);
+        launch_int_sum(c->n_seg, c->seg_rd, c->isum, c->stream);
+        c->x_att_ready = false;
+        c->a_since_c = true;
+    } else if (which == AGIS_X_CALIBRATION) {
+        if (!c->x_cal_ready) return fail(c, AGIS_E_INVALID, "no calibration sums accumulated or set");
+        launch_cal_from_sums(c->n_cal, c->n_days, c->xcal, c->st.pivot_tol, c->dtil, c->cal_rd, c->cal, c->stream);
+        launch_int_sum(c->n_cal, c->cal_rd, c->isum + 1, c->stream);
+        c->x_cal_ready = false;
+        c->a_since_c = false;
+    } else {
+        if (!c->x_frame_ready) return fail(c, AGIS_E_INVALID, "no frame sums accumulated or set");
+        launch_frame_from_sums(c->G, c->n_src, c->src, c->att, c->xframe, c->st.pivot_tol, c->eo, c->stream);
+        c->x_frame_ready = false;
+        c->have_s = false;   // the residuals of the last S block refer to the unrotated frame
+    }
+    record(c, 1);
+    AGIS_CU(c, cudaGetLastError(), "solve");
+    AGIS_CU(c, cudaMemcpyAsync(c->hisum, c->isum, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream), "stats");
+    AGIS_CU(c, cudaMemcpyAsync(c->hstat + 16, c->eo, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "stats");
+    AGIS_CU(c, cudaStreamSynchronize(c->stream), "solve (sync)");
+    if (out) {
+        out->rank_defect = which == AGIS_X_ATTITUDE ? c->hisum[0] : which == AGIS_X_CALIBRATION ? c->hisum[1] : 0;
+        out->elapsed_ms = elapsed(c, 0, 1);
+    }
+    if (which == AGIS_X_FRAME && eps_omega_out)
+        for (int i = 0; i < 6; i++) eps_omega_out[i] = c->hstat[16 + i];
+    return AGIS_OK;
+}
 
 namespace agis {
 // message returned by agis_last_error(NULL) for calls that have no context

@@ -25,6 +25,18 @@ __host__ __device__ inline uint32_t meta_fov(uint32_t m) { return (m >> 6) & 1u;
 __host__ __device__ inline uint32_t meta_kind(uint32_t m) { return (m >> 7) & 1u; }
 __host__ __device__ inline uint32_t meta_cal(uint32_t m) { return m >> 8; }
 
+// Full geometric calibration (Eq. etazeta; agis_config.cal_model = 1): sizes of the parameter
+// layout described in agis.h.  on = 0: the r = 0 offsets of the packed index.
+struct CalGen {
+    int32_t on;
+    int32_t n_gate, j_per_k, col_bin, n_bin, n_k, n_j, al_size;
+    int64_t n_al;                // AL parameters (62 n_gate n_k al_size); the AC groups follow
+    int64_t t0, dt;              // calibration intervals (the short intervals j)
+    double inv_ncol;
+};
+// generic model: gate in bits 8-15 of the packed descriptor (no packed parameter index)
+__host__ __device__ inline uint32_t meta_gate(uint32_t m) { return (m >> 8) & 255u; }
+
 // Geometry passed by value to the kernels.
 struct DevGeo {
     double gamma_half;
@@ -38,6 +50,7 @@ struct DevGeo {
     int64_t t_ep_ns, t_fr_ns, knot0_ns, knot_dt_ns;
     double inv_knot_dt;
     int32_t n_coef;
+    CalGen cg;
 };
 
 inline void fill_devgeo(const agis_geometry* geo, int32_t n_coef, DevGeo& G) {
@@ -379,6 +392,66 @@ __device__ __forceinline__ void qmulf(const float* a, const float* b, float* c) 
     c[3] = -a[0] * b[0] - a[1] * b[1] - a[2] * b[2] + a[3] * b[3];
 }
 
+// Device arrays of the full calibration model's C block (k_calgen.cu).
+struct CalGenWork {
+    const uint32_t* perm;      // observations by (AL cell, bin), then by AC group
+    const int64_t* off;        // n_cells + n_groups + 1 offsets into perm
+    double* V;                 // AL cell: 6 x n_bin, V_j = U_j'^-1 B_j
+    double* E;                 // AL cell: n_bin, sum W per bin
+    double* bs;                // AL cell: n_bin, -sum W R per bin
+    double* cw;                // AL cell: 18 = w_j (6) and the two upper 3x3 factors (6 + 6)
+    double* S;                 // AL group: n_bin x n_bin reduced normals
+    double* r;                 // AL group: n_bin reduced right-hand side
+    double* Et;                // AL group: n_bin, sum of E over the group's cells
+    double* H;                 // AL group: 3 x n_bin Householder vectors of the cc2 columns
+    double* v;                 // AL group: n_bin small-scale update
+    int* idx;                  // AL group: n_bin observed bins (compacted)
+    const double* cc2w;        // 3 x n_bin: sum of L*_r over the columns of each bin
+    double* d;                 // n_cal update
+    int* rd;                   // n_cells + 2 n_groups rank defects (cells, AL groups, AC groups)
+};
+
+// Short interval j and long interval k of an observation time, the AL/AC group (n, g, k) and
+// the shifted Legendre factors L*_1, L*_2 of x = (mu - 13.5) / n_col (Eq. etazeta).
+struct CalPos {
+    int64_t grp;
+    int jj;        // j within its long interval
+    int bin;       // small-scale bin of the nearest column (AL)
+    double L1, L2;
+};
+__device__ __forceinline__ CalPos cal_position(const CalGen& C, int64_t t, uint32_t meta, double mu) {
+    CalPos p;
+    const int64_t rel = t - C.t0;
+    int64_t j = rel < 0 ? 0 : rel / C.dt;
+    if (j > C.n_j - 1) j = C.n_j - 1;
+    const int k = (int)(j / C.j_per_k);
+    p.jj = (int)(j - (int64_t)k * C.j_per_k);
+    p.grp = ((int64_t)meta_ccd(meta) * C.n_gate + meta_gate(meta)) * C.n_k + k;
+    const double x = (mu - 13.5) * C.inv_ncol;
+    p.L1 = 2.0 * x - 1.0;
+    p.L2 = 6.0 * x * x - 6.0 * x + 1.0;
+    int m = (int)floor(mu + 0.5) - 14;
+    m = m < 0 ? 0 : (m > AGIS_N_COL - 1 ? AGIS_N_COL - 1 : m);
+    p.bin = m / C.col_bin;
+    return p;
+}
+
+// The calibration term of an observation line: the r = 0 offset of its packed index, or the
+// full model's sum of Legendre-weighted large-scale terms and the small-scale term.
+__device__ __forceinline__ double cal_term(const DevGeo& G, int64_t t, uint32_t meta, double mu,
+                                           const double* __restrict__ cal) {
+    if (!G.cg.on) return cal[meta_cal(meta)];
+    const CalGen& C = G.cg;
+    const CalPos p = cal_position(C, t, meta, mu);
+    const int f = (int)meta_fov(meta);
+    if (meta_kind(meta) == 0) {
+        const double* c = cal + p.grp * C.al_size + p.jj * 6 + f * 3;
+        return c[0] + p.L1 * c[1] + p.L2 * c[2] + cal[p.grp * C.al_size + 6 * C.j_per_k + p.bin];
+    }
+    const double* c = cal + C.n_al + p.grp * 6 + f * 3;
+    return c[0] + p.L1 * c[1] + p.L2 * c[2];
+}
+
 // Residual and partial derivatives of one observation (FP64).
 //   proper direction: Eqs. astro-standard, roemer, classAberr
 //   field angles: Eqs. srsprop, srsprop1, srspropeta; lines: Eqs. etazeta0, etazeta (r = 0)
@@ -420,7 +493,7 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
     const double us[3] = {dot3(Am, u), dot3(Am + 3, u), dot3(Am + 6, u)};
     const uint32_t fov = meta_fov(meta), kind = meta_kind(meta), ccd = meta_ccd(meta);
     const double f = fov == 0 ? 1.0 : -1.0;
-    const double c_k = cal[meta_cal(meta)];
+    const double c_k = cal_term(G, t, meta, mu, cal);
     const double rho2 = us[0] * us[0] + us[1] * us[1];
     const double irho = rsqrt(rho2);
     const double zeta = atan2_small(us[2], rho2 * irho);

@@ -9,9 +9,10 @@ namespace agis {
 // N_kk = sum W, b_k = -sum W R (dR/dc_k = 1, Eq. pdC); the 1x1 robust solve of
 // Algorithms C.1-C.3 gives d~_k = (b / sqrt(N)) / sqrt(N), or 0 with a rank defect.
 // ---------------------------------------------------------------------------------------
+// sums != NULL: write (N_kk, b_k) pairs there instead of solving
 __global__ void k_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, const int64_t* __restrict__ cal_off,
                             const ObsRec* __restrict__ rec, double tol, double* __restrict__ dtil,
-                            int* __restrict__ rd) {
+                            int* __restrict__ rd, double* __restrict__ sums) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_cal; k += nw) {
@@ -42,6 +43,11 @@ __global__ void k_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, cons
         sw = warp_sum(sw);
         swr = warp_sum(swr);
         if (lane == 0) {
+            if (sums) {
+                sums[2 * (size_t)k] = sw;
+                sums[2 * (size_t)k + 1] = -swr;
+                continue;
+            }
             const double b = -swr;
             if (sw > tol * sw && sw > 0.0) {
                 const double u = sqrt(sw);
@@ -51,6 +57,23 @@ __global__ void k_cal_accum(int n_cal, const uint32_t* __restrict__ perm_c, cons
                 dtil[k] = 0.0;
                 rd[k] = 1;
             }
+        }
+    }
+}
+
+// the 1x1 robust solves from (N_kk, b_k) pairs (the sums of k_cal_accum, reduced over a
+// partition of the sources): same arithmetic as k_cal_accum's own solve
+__global__ void k_cal_solve_sums(int n_cal, const double* __restrict__ sums, double tol, double* __restrict__ dtil,
+                                 int* __restrict__ rd) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_cal; k += gridDim.x * blockDim.x) {
+        const double sw = sums[2 * (size_t)k], b = sums[2 * (size_t)k + 1];
+        if (sw > tol * sw && sw > 0.0) {
+            const double u = sqrt(sw);
+            dtil[k] = (b / u) / u;
+            rd[k] = 0;
+        } else {
+            dtil[k] = 0.0;
+            rd[k] = 1;
         }
     }
 }
@@ -84,7 +107,25 @@ void launch_cal(int n_cal, int n_days, const uint32_t* perm_c, const int64_t* ca
     int blocks = (n_cal + wpb - 1) / wpb;
     if (blocks > 152 * sh.cal_bps) blocks = 152 * sh.cal_bps;
     if (blocks < 1) blocks = 1;
-    k_cal_accum<<<blocks, sh.cal_threads, 0, s>>>(n_cal, perm_c, cal_off, rec, tol, dtil, rd);
+    k_cal_accum<<<blocks, sh.cal_threads, 0, s>>>(n_cal, perm_c, cal_off, rec, tol, dtil, rd, nullptr);
+    k_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal);
+}
+
+// partitioned sources: the local (N_kk, b_k) sums, and the update from reduced sums
+void launch_cal_sums(int n_cal, const uint32_t* perm_c, const int64_t* cal_off, const ObsRec* rec, double* sums,
+                     const Shapes& sh, cudaStream_t s) {
+    const int wpb = sh.cal_threads / 32;
+    int blocks = (n_cal + wpb - 1) / wpb;
+    if (blocks > 152 * sh.cal_bps) blocks = 152 * sh.cal_bps;
+    if (blocks < 1) blocks = 1;
+    k_cal_accum<<<blocks, sh.cal_threads, 0, s>>>(n_cal, perm_c, cal_off, rec, 0.0, nullptr, nullptr, sums);
+}
+void launch_cal_from_sums(int n_cal, int n_days, const double* sums, double tol, double* dtil, int* rd, double* cal,
+                          cudaStream_t s) {
+    int blocks = (n_cal + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_cal_solve_sums<<<blocks, 256, 0, s>>>(n_cal, sums, tol, dtil, rd);
     k_cal_project<<<(3 * n_days + 127) / 128, 128, 0, s>>>(n_days, dtil, cal);
 }
 
@@ -262,6 +303,29 @@ __global__ void k_frame_apply_att(DevGeo G, double* __restrict__ att, const doub
     double* a = att + 4 * (int64_t)n;
     qmul(fi, a, o);
     a[0] = o[0]; a[1] = o[1]; a[2] = o[2]; a[3] = o[3];
+}
+
+// the 27 frame sums of the local sources (the block partials added in order)
+__global__ void k_frame_sum(int n_part, const double* __restrict__ partial, double* __restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x >= kFrameVals) return;
+    double v = 0.0;
+    for (int p = 0; p < n_part; p++) v += partial[p * kFrameVals + threadIdx.x];
+    out[threadIdx.x] = v;
+}
+
+void launch_frame_sums(int n, const int32_t* subset, const double* src, const double* ref, const DevGeo& G,
+                       double* partial, int n_part, double* sums, cudaStream_t s) {
+    const double tt = (double)(G.t_ep_ns - G.t_fr_ns) * 1e-9 / G.year_s;
+    k_frame_normals<<<n_part, 256, 0, s>>>(n, subset, src, ref, tt, partial);
+    k_frame_sum<<<1, 32, 0, s>>>(n_part, partial, sums);
+}
+// solve from reduced sums (one part) and apply to the local sources and the attitude
+void launch_frame_from_sums(const DevGeo& G, int n_src, double* src, double* att, const double* sums, double tol,
+                            double* eo, cudaStream_t s) {
+    const double tt = (double)(G.t_ep_ns - G.t_fr_ns) * 1e-9 / G.year_s;
+    k_frame_solve<<<1, 32, 0, s>>>(1, sums, tol, eo);
+    k_frame_apply_src<<<(n_src + 255) / 256, 256, 0, s>>>(n_src, src, eo, tt);
+    k_frame_apply_att<<<(G.n_coef + 255) / 256, 256, 0, s>>>(G, att, eo);
 }
 
 void launch_frame(const DevGeo& G, int n, const int32_t* subset, int n_src, double* src, const double* ref,

@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(256) k_mix_forward(DevGeo G, int64_t n_obs, co
         const int64_t t = t_ns[o];
         const uint32_t m = meta[o];
         ObsOut ob;
-        observe<2>(G, S, t, m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
+        observe<2>(G, S, t, m, (G.cg.on || meta_kind(m)) ? mu[o] : 0.0, att, cal, ob);
         MixS a;
         float2 R;
         split_pair(ob.R, R.x, R.y);

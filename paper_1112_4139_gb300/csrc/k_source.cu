@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, AttNoise an, int6
         S.par = g[9]; S.pma = g[10]; S.pmd = g[11]; S.cosd = g[12];
         const int64_t t = t_ns[o];
         const uint32_t m = meta[o];
-        const double muv = meta_kind(m) ? mu[o] : 0.0;
+        const double muv = (G.cg.on || meta_kind(m)) ? mu[o] : 0.0;
         ObsOut ob;
         observe<1>(G, S, t, m, muv, att, cal, ob);
         const double sg = (double)sigma[o];
@@ -561,7 +561,7 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
         source_geo(src + 5 * (size_t)obs_src[o], S);
         uint32_t m = meta[o];
         ObsOut ob;
-        observe<0>(G, S, t_ns[o], m, meta_kind(m) ? mu[o] : 0.0, att, cal, ob);
+        observe<0>(G, S, t_ns[o], m, (G.cg.on || meta_kind(m)) ? mu[o] : 0.0, att, cal, ob);
         R[o] = ob.R;
     }
 }

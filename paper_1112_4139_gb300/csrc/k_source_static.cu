@@ -360,6 +360,8 @@ extern "C" int agis_source_update_static(const agis_geometry* geo, const agis_co
     if (n_obs < 0 || n_src < 0) return err(AGIS_E_INVALID, "negative size");
     if (n_obs > 0 && (!obs->t_ns || !obs->src || !obs->ccd || !obs->fov || !obs->kind || !obs->sigma || !obs->mu))
         return err(AGIS_E_INVALID, "null observation array");
+    if (cfg->cal_model != 0)
+        return err(AGIS_E_INVALID, "the static source update takes the r = 0 calibration offsets only (cal_model 0)");
     if (max_obs_per_source < 1 || max_obs_per_source > AGIS_STATIC_MAX_OBS)
         return err(AGIS_E_INVALID, "max_obs_per_source must be in 1..AGIS_STATIC_MAX_OBS (" +
                                        std::to_string(AGIS_STATIC_MAX_OBS) + ")");
