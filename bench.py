@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--tune-iters", type=int, default=20,
                     help="iterations of the launch-shape autotuner before the warm-up (0: default shapes)")
     ap.add_argument("--knot-dt-s", type=int, default=0, help="override the attitude knot interval (testing)")
+    ap.add_argument("--cal-generic", action="store_true",
+                    help="the full geometric calibration model (two gates, 30-day long intervals, binned columns)")
+    ap.add_argument("--cal-col-bin", type=int, default=16, help="--cal-generic: AC pixel columns per bin")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the wall-time-to-1-uas runs that the default line carries")
     ap.add_argument("--convergence", action="store_true",
@@ -216,95 +219,125 @@ def _obs_subset(ds, sel):
                                gate=take(ds.gate))
 
 
-def cpu_baseline(ds, seconds=20.0, workers=None):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload, scaled to
+def _src_range(ds, off, i0, i1):
+    """The sources i0..i1-1 (contiguous) with their observations, renumbered from 0 (the
+    observations are sorted by source, so this is one slice)."""
+    import dataclasses
+    sl = slice(int(off[i0]), int(off[i1]))
+    take = lambda a: np.ascontiguousarray(a[sl])  # noqa: E731
+    return dataclasses.replace(ds, t_ns=take(ds.t_ns), src=(take(ds.src) - i0).astype(np.int32), ccd=take(ds.ccd),
+                               fov=take(ds.fov), kind=take(ds.kind), sigma=take(ds.sigma), mu=take(ds.mu),
+                               noise=take(ds.noise), gate=take(ds.gate), src_true=ds.src_true[i0:i1].copy(),
+                               src_mag=ds.src_mag[i0:i1].copy(), n_transits=ds.n_transits[i0:i1].copy(),
+                               src0=ds.src0[i0:i1].copy())
+
+
+class OracleSampler:
+    """The FP64 oracle on the host cores, on bounded samples of the workload, scaled to
     observations/s per iteration.  Pieces of the iteration are independent (sources in the S
     block, segments in the A block, intervals in the C block) and run in a pool of worker
-    processes (spawn start, one per core, single-threaded BLAS): S on batches of 50 sampled
-    sources for about half the budget, A on as many segments (all observations of their time
-    range) as there are workers, C on as many calibration intervals.  The iteration time is
-    the observations / throughput of each block; the single-core figure comes from the mean
-    time per task of the same runs."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    import oracle.blocks as OB
-    import oracle.model as OM
-    workers = workers or min(16, os.cpu_count() or 1)
-    P = OM.problem_from_dataset(ds)
-    st = OB.Settings(seg_len=2880 if ds.geometry["knot_dt_ns"] == 30_000_000_000 else 720, seg_overlap=12)
-    rng = np.random.default_rng(0)
-    order = rng.permutation(ds.n_src)
-    segs = OB.segments(P, st)
-    kn = P.knots()
-    days = ds.geometry["n_cal_days"]
-    cday = OM.cal_day(P, ds.t_ns)
-    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in env_keep:
-        os.environ[k] = "1"
-    try:
-        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-            list(ex.map(_oracle_task, ["S"] * workers, [(ds.subset_sources(order[:2]), st)] * workers))  # start-up
-            # S: batches of 50 sources for about half the budget
-            t0 = time.perf_counter()
-            futs, nxt, n_s, t_s_tasks, n_tasks = [], 0, 0, 0.0, 0
-            while time.perf_counter() - t0 < 0.5 * seconds and nxt < ds.n_src:
-                while len(futs) < 2 * workers and nxt < ds.n_src:
-                    futs.append(ex.submit(_oracle_task, "S", (ds.subset_sources(np.sort(order[nxt:nxt + 50])), st)))
-                    nxt += 50
-                done, pending = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
-                for f in done:
-                    n, dt = f.result()
-                    n_s += n
-                    t_s_tasks += dt
-                    n_tasks += 1
-                futs = list(pending)
-            for f in futs:
-                n, dt = f.result()
-                n_s += n
-                t_s_tasks += dt
-                n_tasks += 1
-            thr_s = n_s / (time.perf_counter() - t0)
-            thr_s1 = n_s / t_s_tasks
-            n_src_done = min(nxt, ds.n_src)
-            # A: one segment per worker, spread over the mission
-            pick = np.linspace(0, len(segs) - 1, min(workers, len(segs))).astype(int)
-            tasks = []
-            for k in pick:
-                l_lo, l_hi = segs[k][0], segs[k][1]
-                sel = np.nonzero((ds.t_ns >= kn[l_lo]) & (ds.t_ns < kn[l_hi + 1]))[0]
-                tasks.append((_obs_subset(ds, sel), st, l_lo, l_hi))
-            t1 = time.perf_counter()
-            res_a = list(ex.map(_oracle_task, ["A"] * len(tasks), tasks))
-            thr_a = len(tasks) / (time.perf_counter() - t1)
-            thr_a1 = len(tasks) / sum(r[1] for r in res_a)
-            n_a = int(np.mean([r[0] for r in res_a]))
-            # C: one calibration interval per worker
-            pick = np.linspace(0, days - 1, min(workers, days)).astype(int)
-            tasks = [_obs_subset(ds, np.nonzero(cday == d)[0]) for d in pick]
-            t2 = time.perf_counter()
-            res_c = list(ex.map(_oracle_task, ["C"] * len(tasks), tasks))
-            thr_c = len(tasks) / (time.perf_counter() - t2)
-            thr_c1 = len(tasks) / sum(r[1] for r in res_c)
-    finally:
-        for k, v in env_keep.items():
+    processes (spawn start, one per core, single-threaded BLAS).  A sample: S on runs of 50
+    consecutive sources from random places for a time budget, A on some segments (all
+    observations of their time range, spread over the mission), C on some calibration
+    intervals.  The iteration time is the observations / throughput of each block; the
+    single-core figure comes from the summed task times of the same runs."""
+
+    def __init__(self, ds, workers=None, n_seg=None, n_day=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import oracle.blocks as OB
+        import oracle.model as OM
+        self.ds = ds
+        self.workers = workers or min(16, os.cpu_count() or 1)
+        P = OM.problem_from_dataset(ds)
+        self.st = OB.Settings(seg_len=2880 if ds.geometry["knot_dt_ns"] == 30_000_000_000 else 720, seg_overlap=12)
+        self.off = ds.src_offsets()
+        self.starts = np.random.default_rng(0).permutation(max(1, ds.n_src // 50)) * 50
+        self.next_start = 0
+        self.segs = OB.segments(P, self.st)
+        kn = P.knots()
+        self.days = ds.geometry["n_cal_days"]
+        n_seg = n_seg or self.workers
+        n_day = n_day or self.workers
+        pick_a = np.linspace(0, len(self.segs) - 1, min(n_seg, len(self.segs))).astype(int)
+        pick_c = np.linspace(0, self.days - 1, min(n_day, self.days)).astype(int)
+        t = time.perf_counter()
+        self.args_a = [(_obs_subset(ds, np.nonzero((ds.t_ns >= kn[self.segs[k][0]]) &
+                                                   (ds.t_ns < kn[self.segs[k][1] + 1]))[0]),
+                        self.st, self.segs[k][0], self.segs[k][1]) for k in pick_a]
+        day = OM.cal_day(P, ds.t_ns)
+        self.args_c = [_obs_subset(ds, np.nonzero(day == d)[0]) for d in pick_c]
+        self.t_select = time.perf_counter() - t
+        self.env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in self.env_keep:
+            os.environ[k] = "1"
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"))
+        warm = _src_range(ds, self.off, 0, min(2, ds.n_src))
+        list(self.ex.map(_oracle_task, ["S"] * self.workers, [(warm, self.st)] * self.workers))  # start-up
+
+    def close(self):
+        self.ex.shutdown()
+        for k, v in self.env_keep.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    t_iter = ds.n_obs / thr_s + len(segs) / thr_a + days / thr_c
-    t_iter1 = ds.n_obs / thr_s1 + len(segs) / thr_a1 + days / thr_c1
-    sample = (f"S block on {n_src_done} sampled sources ({n_s} obs, {n_tasks} batches of 50), A block on "
-              f"{len(res_a)} of {len(segs)} segments (~{n_a} obs each), C block on {len(res_c)} of {days} "
-              f"intervals, in {workers} worker processes; per-iteration time extrapolated to {ds.n_obs} obs = "
-              f"{t_iter:.1f} s ({t_iter1:.1f} s on one core)")
-    cpu = ""
+
+    def step(self, s_seconds, n_seg, n_day):
+        import concurrent.futures as cf
+        ds, ex, st = self.ds, self.ex, self.st
+        t0 = time.perf_counter()
+        futs, n_s, t_s_tasks, n_tasks = [], 0, 0.0, 0
+        while time.perf_counter() - t0 < s_seconds or n_tasks == 0:
+            while len(futs) < 2 * self.workers:
+                i0 = int(self.starts[self.next_start % self.starts.size])
+                self.next_start += 1
+                futs.append(ex.submit(_oracle_task, "S", (_src_range(ds, self.off, i0, min(ds.n_src, i0 + 50)), st)))
+            done, pending = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in done:
+                n, dt = f.result()
+                n_s, t_s_tasks, n_tasks = n_s + n, t_s_tasks + dt, n_tasks + 1
+            futs = list(pending)
+        for f in futs:
+            n, dt = f.result()
+            n_s, t_s_tasks, n_tasks = n_s + n, t_s_tasks + dt, n_tasks + 1
+        thr_s = n_s / (time.perf_counter() - t0)
+        thr_s1 = n_s / t_s_tasks
+        args_a = self.args_a[:n_seg]
+        t1 = time.perf_counter()
+        res_a = list(ex.map(_oracle_task, ["A"] * len(args_a), args_a))
+        thr_a = len(args_a) / (time.perf_counter() - t1)
+        thr_a1 = len(args_a) / sum(r[1] for r in res_a)
+        args_c = self.args_c[:n_day]
+        t2 = time.perf_counter()
+        res_c = list(ex.map(_oracle_task, ["C"] * len(args_c), args_c))
+        thr_c = len(args_c) / (time.perf_counter() - t2)
+        thr_c1 = len(args_c) / sum(r[1] for r in res_c)
+        t_iter = ds.n_obs / thr_s + len(self.segs) / thr_a + self.days / thr_c
+        t_iter1 = ds.n_obs / thr_s1 + len(self.segs) / thr_a1 + self.days / thr_c1
+        sample = (f"S block on {50 * n_tasks} sources ({n_s} obs, {n_tasks} runs of 50 consecutive sources from "
+                  f"random places), A block on {len(res_a)} of {len(self.segs)} segments "
+                  f"(~{int(np.mean([r[0] for r in res_a]))} obs each), C block on {len(res_c)} of {self.days} "
+                  f"intervals, in {self.workers} worker processes; per-iteration time extrapolated to {ds.n_obs} obs "
+                  f"= {t_iter:.1f} s ({t_iter1:.1f} s on one core); sample selection {self.t_select:.1f} s, not counted")
+        cpu = ""
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            cpu = next((ln.split(":", 1)[1].strip() for ln in out.splitlines() if ln.startswith("Model name")), "")
+        except OSError:
+            pass
+        return {"value": ds.n_obs / t_iter, "unit": "obs/s", "cores": self.workers, "kind": "oracle", "sample": sample,
+                "single_core_value": ds.n_obs / t_iter1, "cpu_model": cpu, "host_cores": os.cpu_count()}
+
+
+def cpu_baseline(ds, seconds=20.0, workers=None):
+    """One sample of OracleSampler: S for half the budget, A on one segment and C on one
+    interval per worker."""
+    smp = OracleSampler(ds, workers)
     try:
-        cpu = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
-        cpu = next((ln.split(":", 1)[1].strip() for ln in cpu.splitlines() if ln.startswith("Model name")), "")
-    except OSError:
-        pass
-    return {"value": ds.n_obs / t_iter, "unit": "obs/s", "cores": workers, "kind": "oracle", "sample": sample,
-            "single_core_value": ds.n_obs / t_iter1, "cpu_model": cpu, "host_cores": os.cpu_count()}
+        return smp.step(0.5 * seconds, smp.workers, smp.workers)
+    finally:
+        smp.close()
 
 
 def make_dataset(args):
@@ -314,6 +347,9 @@ def make_dataset(args):
         over["n_src"] = args.n_src
     if args.knot_dt_s:
         over["knot_dt_s"] = args.knot_dt_s
+    if args.cal_generic:
+        # the full geometric calibration: two gates, 30-day long intervals, 16-column bins
+        over.update(cal_generic=True, n_gate=2, cal_j_per_k=30, cal_col_bin=args.cal_col_bin)
     t = time.perf_counter()
     ds = synth.simulate(synth.config(args.workload, **over))
     return ds, time.perf_counter() - t
@@ -324,10 +360,17 @@ def run_reference(args, rank, world):
         return
     ds, _ = make_dataset(args)
     vals = []
-    for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(ds, seconds=max(6.0, 90.0 / max(1, args.warmup + args.steps)))
-        if k >= args.warmup:
-            vals.append(cb)
+    # one pool and sample selection for the run; each step a bounded sample (S for a few
+    # seconds, A on a few segments, C on a few intervals), the whole run within a few minutes
+    n_steps = max(1, args.warmup + args.steps)
+    smp = OracleSampler(ds, n_seg=4, n_day=4)
+    try:
+        for k in range(n_steps):
+            cb = smp.step(max(2.0, 60.0 / n_steps), 4, 4)
+            if k >= args.warmup:
+                vals.append(cb)
+    finally:
+        smp.close()
     v = float(np.median([c["value"] for c in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
@@ -676,7 +719,11 @@ def main():
     an_ns = int(round(args.attnoise_s * 1e9))
     if an_ns > 0 and (head != "fp64" or not args.single_form):
         raise SystemExit("--attnoise-s needs --precision fp64 --single-form")
-    cfgs = {k: agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, **v) for k, v in forms.items()}
+    if args.cal_generic and not (args.single_form and head == "fp64"):
+        raise SystemExit("--cal-generic needs --precision fp64 --single-form (the full calibration is FP64 only)")
+    calc = agis.calibration_config(ds.geometry)
+    cfgs = {k: agis.default_config(seg_len=seg_len, use_graph=1, frame_each_iter=1, **calc, **v)
+            for k, v in forms.items()}
     # the mixed form is timed over whole refresh cycles, so its per-iteration time includes
     # the full FP64 evaluation at its share
     cyc = max(1, args.refresh_every)
@@ -763,7 +810,9 @@ def main():
                    "l2": "no flush: inputs (tens of GB) exceed the 129 MB L2", "graph": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "t_generate_s": round(t_gen, 1), "t_init_s": round(r["t_init"], 2),
-                   "autotune": r["tuning"], "attnoise_bucket_s": args.attnoise_s or None},
+                   "autotune": r["tuning"], "attnoise_bucket_s": args.attnoise_s or None,
+                   "calibration": ({"model": "full (Eq. etazeta)", "n_gate": 2, "j_per_k": 30,
+                                    "col_bin": args.cal_col_bin} if args.cal_generic else "r = 0 offsets per day")},
         "e2e": ({"value": e2e, "unit": "obs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
                 if e2e is not None else None),
         "gpu_launches": (KERNELS_PER_STEP[head][0] * r["n_full_eval"] +

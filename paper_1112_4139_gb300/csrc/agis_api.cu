@@ -14,11 +14,11 @@
 namespace agis {
 void launch_obs_pass(const DevGeo& G, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
-                     const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
+                     const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch, uint64_t* skey,
                      const Shapes& sh, cudaStream_t stream);
 void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
                          const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
-                         int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream);
+                         const uint64_t* skey, int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream);
 void launch_evaluate(const DevGeo& G, const int64_t* t_ns, const uint32_t* meta, const double* mu,
                      const int32_t* obs_src, int64_t n_obs, const double* src, const double* att, const double* cal,
                      double* R, cudaStream_t stream);
@@ -297,6 +297,7 @@ struct agis_ctx {
     bool mix_stale = true;   // the records do not describe the current state: evaluate in full
     int mix_since = 0;       // source updates since the last full evaluation
     double* scratch = nullptr;   // n_obs x 8 doubles, source order
+    uint64_t* skey = nullptr;    // n_obs sort keys of h / sigma (the robust scale's selects), source order
     double* sgeo = nullptr;      // n_src x 16
     int cap = 0, n_sblocks = 0;
     int* work = nullptr;
@@ -533,7 +534,7 @@ void enqueue_s_pass(agis_ctx* c, bool refresh) {
                         c->stream);
     else
         launch_obs_pass(c->G, c->an, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
-                        c->cal, c->rec, c->sgeo, c->scratch, c->sh, c->stream);
+                        c->cal, c->rec, c->sgeo, c->scratch, c->skey, c->sh, c->stream);
 }
 void enqueue_s_solve(agis_ctx* c) {
     if (c->mixed)
@@ -541,7 +542,7 @@ void enqueue_s_solve(agis_ctx* c) {
                          c->stream);
     else
         launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
-                            c->work, c->n_sblocks, c->sh, c->stream);
+                            c->skey, c->work, c->n_sblocks, c->sh, c->stream);
     // excess attitude noise from the residuals of this source update, and the attitude weights
     if (c->an.eps2)
         launch_an_estimate(c->n_obs, c->an, c->an_max_run, c->an_eps2, c->an_perm, c->an_off, c->rec, c->sigma,
@@ -1035,7 +1036,9 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
             (rc = dalloc(c, &c->mw.sums, n_src)))
             return bail(rc);
     } else {
-        if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr))) return bail(rc);
+        if ((rc = dalloc(c, &c->rec, n)) || (rc = dalloc(c, &c->scratch, (size_t)n * kScr)) ||
+            (rc = dalloc(c, &c->skey, n)))
+            return bail(rc);
         if (cfg->block_order == 1) {
             if ((rc = dalloc(c, &c->datt64, 4 * (size_t)n_coef))) return bail(rc);
             cudaMemsetAsync(c->datt64, 0, sizeof(double) * 4 * (size_t)n_coef, s);

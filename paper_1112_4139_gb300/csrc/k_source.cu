@@ -13,9 +13,11 @@ namespace agis {
 
 
 
-// k-th smallest (0-based) of the keys stored in scr[j*kScr + 6] (as bit patterns), j < n,
-// by an 8-pass radix select with a 256-bin shared-memory histogram per warp.
-__device__ uint64_t warp_select(const double* scr, int n, int k, int* hist, int lane) {
+// k-th smallest (0-based) of the keys[0..n) (order-preserving maps of h / sigma, one 8-byte key
+// per observation, contiguous) by a radix select of 8-bit digits with a 256-bin shared-memory
+// histogram per warp.  A pass whose chosen digit holds a single key ends the select: one more
+// pass finds that key (on continuous data about 4 passes instead of 8).
+__device__ uint64_t warp_select(const uint64_t* __restrict__ keys, int n, int k, int* hist, int lane) {
     uint64_t prefix = 0, pmask = 0;
     int kk = k;
     for (int d = 7; d >= 0; d--) {
@@ -24,7 +26,7 @@ __device__ uint64_t warp_select(const double* scr, int n, int k, int* hist, int 
         for (int i = 0; i < 8; i++) hist[lane * 8 + i] = 0;
         __syncwarp();
         for (int j = lane; j < n; j += kWarp) {
-            uint64_t key = (uint64_t)__double_as_longlong(scr[(size_t)j * kScr + 6]);
+            const uint64_t key = keys[j];
             if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
         }
         __syncwarp();
@@ -42,7 +44,7 @@ __device__ uint64_t warp_select(const double* scr, int n, int k, int* hist, int 
         int excl = incl - tot;
         unsigned ball = __ballot_sync(0xffffffffu, incl > kk);
         int src_lane = __ffs(ball) - 1;
-        int bin = 0, below = 0;
+        int bin = 0, below = 0, cnt = 0;
         if (lane == src_lane) {
             int acc = excl;
             int bsel = 7;
@@ -53,26 +55,43 @@ __device__ uint64_t warp_select(const double* scr, int n, int k, int* hist, int 
             }
             bin = lane * 8 + bsel;
             below = acc;
+            cnt = hist[bin];
         }
         bin = __shfl_sync(0xffffffffu, bin, src_lane);
         below = __shfl_sync(0xffffffffu, below, src_lane);
+        cnt = __shfl_sync(0xffffffffu, cnt, src_lane);
         kk -= below;
         prefix |= (uint64_t)bin << shift;
         pmask |= (uint64_t)0xffu << shift;
         __syncwarp();
+        if (cnt == 1 && d > 0) {
+            // the only key with this prefix is the k-th smallest
+            uint64_t found = 0;
+            for (int j = lane; j < n; j += kWarp) {
+                const uint64_t key = keys[j];
+                if ((key & pmask) == prefix) found = key;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t v = __shfl_xor_sync(0xffffffffu, found, o);
+                found = v > found ? v : found;
+            }
+            return found;
+        }
     }
     return prefix;
 }
 
 // the (k)-th and (k+1)-th smallest values (k+1 capped at n-1)
-__device__ void warp_select_pair(const double* scr, int n, int k, int* hist, int lane, double& v0, double& v1) {
-    uint64_t K = warp_select(scr, n, k, hist, lane);
+__device__ void warp_select_pair(const uint64_t* __restrict__ keys, int n, int k, int* hist, int lane, double& v0,
+                                 double& v1) {
+    uint64_t K = warp_select(keys, n, k, hist, lane);
     v0 = dkey_inv(K);
     if (k + 1 >= n) { v1 = v0; return; }
     int less = 0, eq = 0;
     uint64_t nxt = ~0ull;
     for (int j = lane; j < n; j += kWarp) {
-        uint64_t key = (uint64_t)__double_as_longlong(scr[(size_t)j * kScr + 6]);
+        const uint64_t key = keys[j];
         less += key < K;
         eq += key == K;
         if (key > K && key < nxt) nxt = key;
@@ -233,7 +252,7 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, AttNoise an, int6
                                                      const int32_t* __restrict__ obs_src,
                                                      const double* __restrict__ geo, const double* __restrict__ att,
                                                      const double* __restrict__ cal, double* __restrict__ scr,
-                                                     ObsRec* __restrict__ rec) {
+                                                     uint64_t* __restrict__ skey, ObsRec* __restrict__ rec) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
         const double* g = geo + 16 * (size_t)obs_src[o];
         SrcGeo S;
@@ -253,7 +272,7 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, AttNoise an, int6
         double* e = scr + (size_t)o * kScr;
         e[0] = ob.R;
         e[1] = ob.A[0]; e[2] = ob.A[1]; e[3] = ob.A[2]; e[4] = ob.A[3]; e[5] = ob.A[4];
-        e[6] = __longlong_as_double((long long)dkey(x));
+        skey[o] = dkey(x);
         e[7] = s2;
         ObsRec* r = rec + o;
         r->t_ns = t;
@@ -356,7 +375,8 @@ constexpr int kSolveWarps = 2;
 __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
     Settings st, const uint32_t* __restrict__ meta, const int64_t* __restrict__ src_off,
     const int32_t* __restrict__ src_nal, const int32_t* __restrict__ src_order, int32_t n_src, int batch,
-    SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch, int* work_counter) {
+    SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch, const uint64_t* __restrict__ skey,
+    int* work_counter) {
     __shared__ int hist_all[kSolveWarps * 256];
     __shared__ ClassSums sums_all[kSolveWarps][kWarp];
     const int lane = threadIdx.x & 31;
@@ -410,8 +430,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                 const double h1 = p1 * (double)(n - 1), h5 = p5 * (double)(n - 1);
                 const int lo1 = (int)floor(h1), lo5 = (int)floor(h5);
                 double a0, a1, b0, b1;
-                warp_select_pair(scr, n, lo1, hist, lane, a0, a1);
-                warp_select_pair(scr, n, lo5, hist, lane, b0, b1);
+                warp_select_pair(skey + o0, n, lo1, hist, lane, a0, a1);
+                warp_select_pair(skey + o0, n, lo5, hist, lane, b0, b1);
                 vs = 0.5 * ((b0 + (h5 - lo5) * (b1 - b0)) - (a0 + (h1 - lo1) * (a1 - a0)));
                 __syncwarp();
             }
@@ -570,19 +590,20 @@ __global__ void k_evaluate(DevGeo G, const int64_t* __restrict__ t_ns, const uin
 void launch_obs_pass(const DevGeo& G, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
                      const double* mu, const int32_t* obs_src, int64_t n_obs, int32_t n_src, const double* src,
                      const double* att, const double* cal, ObsRec* rec, double* geo, double* scratch,
-                     const Shapes& sh, cudaStream_t stream) {
+                     uint64_t* skey, const Shapes& sh, cudaStream_t stream) {
     k_src_geo<<<(n_src + 255) / 256 > 0 ? (n_src + 255) / 256 : 1, 256, 0, stream>>>(n_src, src, geo);
     const int th = sh.obs_threads;
     int64_t fb = (n_obs + th - 1) / th;
     if (fb > 152 * (int64_t)sh.obs_bps) fb = 152 * (int64_t)sh.obs_bps;
     if (fb < 1) fb = 1;
-    k_obs_forward<<<(int)fb, th, 0, stream>>>(G, an, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, rec);
+    k_obs_forward<<<(int)fb, th, 0, stream>>>(G, an, n_obs, t_ns, meta, sigma, mu, obs_src, geo, att, cal, scratch, skey,
+                                              rec);
 }
 
 // the per-source solves of the S block on the scratch rows of the observation pass
 void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t* src_off, const int32_t* src_nal,
                          const int32_t* src_order, int32_t n_src, const SrcOutPtrs& out, ObsRec* rec, double* scratch,
-                         int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream) {
+                         const uint64_t* skey, int* work_counter, int n_blocks, const Shapes& sh, cudaStream_t stream) {
     cudaMemsetAsync(work_counter, 0, sizeof(int), stream);
     // batch size: 32 sources per warp when there are enough sources to keep ~16 warps per SM
     // busy, unless the autotuner chose one
@@ -594,7 +615,7 @@ void launch_source_solve(const Settings& st, const uint32_t* meta, const int64_t
     if (blocks > n_blocks * 4) blocks = n_blocks * 4;
     if (blocks < 1) blocks = 1;
     k_source_solve<<<blocks, 32 * kSolveWarps, 0, stream>>>(st, meta, src_off, src_nal, src_order, n_src, batch, out,
-                                                            rec, scratch, work_counter);
+                                                            rec, scratch, skey, work_counter);
 }
 
 void launch_src_geo(int32_t n_src, const double* src, double* geo, cudaStream_t s) {
