@@ -604,6 +604,12 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
 // ---------------------------------------------------------------------------------------
 __host__ __device__ constexpr int up5(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i); }
 
+// U holds the 15 upper-packed entries of the factor, then the reciprocals of its 5 diagonal
+// entries (0 where the pivot test failed): each pivot takes one reciprocal square root, and the
+// off-diagonal entries and both substitutions multiply by the stored reciprocals instead of
+// dividing (equal to the divisions up to rounding).
+constexpr int kU5 = 20;
+
 __device__ __forceinline__ int chol5(const double* N, double* U, double tol) {
     int d = 0;
 #pragma unroll
@@ -614,14 +620,17 @@ __device__ __forceinline__ int chol5(const double* N, double* U, double tol) {
 #pragma unroll
             for (int k = 0; k < i; k++) s += U[up5(k, i)] * U[up5(k, j)];
             if (i < j) {
-                double uii = U[up5(i, i)];
-                U[up5(i, j)] = uii > 0.0 ? (N[up5(i, j)] - s) / uii : 0.0;
+                const double ri = U[15 + i];
+                U[up5(i, j)] = ri > 0.0 ? (N[up5(i, j)] - s) * ri : 0.0;
             } else {
                 double v = N[up5(j, j)] - s;
                 if (v > tol * N[up5(j, j)]) {
-                    U[up5(j, j)] = sqrt(v);
+                    const double r = rsqrt(v);
+                    U[up5(j, j)] = v * r;
+                    U[15 + j] = r;
                 } else {
                     U[up5(j, j)] = 0.0;
+                    U[15 + j] = 0.0;
                     d++;
                 }
             }
@@ -637,14 +646,14 @@ __device__ __forceinline__ void chol5_solve(const double* U, const double* b, do
         double s = b[i];
 #pragma unroll
         for (int k = 0; k < i; k++) s -= U[up5(k, i)] * y[k];
-        y[i] = U[up5(i, i)] > 0.0 ? s / U[up5(i, i)] : 0.0;
+        y[i] = U[15 + i] > 0.0 ? s * U[15 + i] : 0.0;
     }
 #pragma unroll
     for (int i = 4; i >= 0; i--) {
         double s = y[i];
 #pragma unroll
         for (int k = i + 1; k < 5; k++) s -= U[up5(i, k)] * x[k];
-        x[i] = U[up5(i, i)] > 0.0 ? s / U[up5(i, i)] : 0.0;
+        x[i] = U[15 + i] > 0.0 ? s * U[15 + i] : 0.0;
     }
 }
 

@@ -410,7 +410,7 @@ __device__ __noinline__ void mix_solve_general(const Settings& st, int i, int n,
     }
     __syncwarp();
     double d[5] = {0, 0, 0, 0, 0};
-    double U[15];
+    double U[kU5];
     double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
     int nu = 0, nout = 0, rd = 0;
     const int rounds = st.robust ? st.n_rounds + 1 : 1;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) k_mix_solve5(Settings st, int last, const
     const int nout = rsum.nout;
     SrcRound in = w.round[i];
     const double tol_piv = fmax(st.pivot_tol, kMixPivotTol);
-    double U[15], dl[5], Q, S2;
+    double U[kU5], dl[5], Q, S2;
     int rd;
     const int nu = n - nout - 5;
     double y = 0.0;

@@ -298,7 +298,7 @@ __device__ __noinline__ void solve_general(const Settings& st, int i, int64_t o0
     }
     __syncwarp();
     double d[5] = {0, 0, 0, 0, 0};
-    double U[15];
+    double U[kU5];
     double y = 0.0, Q = 0.0, Q0 = 0.0;
     int nu = 0, nout = 0, rd = 0;
     const int rounds = st.robust ? st.n_rounds + 1 : 1;
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
         }
         // ---- inner iteration, class-sum path (lane k solves source k)
         double d[5] = {0, 0, 0, 0, 0};
-        double U[15];
-        for (int q = 0; q < 15; q++) U[q] = 0.0;
+        double U[kU5];
+        for (int q = 0; q < kU5; q++) U[q] = 0.0;
         double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
         int nu = 0, nout = 0, rd = 0;
         for (int rnd = 0; rnd < rounds; rnd++) {

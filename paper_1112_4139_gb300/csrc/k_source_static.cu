@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(128) k_source_static(DevGeo G, Settings st, Ob
             for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
         }
         __syncwarp();
-        double d[5] = {0, 0, 0, 0, 0}, U[15], N[15], b[5];
+        double d[5] = {0, 0, 0, 0, 0}, U[kU5], N[15], b[5];
         double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
         int nu = 0, nout = 0;
         const int rounds = st.robust ? st.n_rounds + 1 : 1;
