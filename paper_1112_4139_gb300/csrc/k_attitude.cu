@@ -326,13 +326,24 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
             if (sub == 0) yv[base + r] = yr;
         }
         // the window below the pivot row: W[a][b] -= V_a W[0][b] (= W[0][a] W[0][b] / D_r);
-        // row r's slot is not written in this step
+        // row r's slot is not written in this step.  All 45 operands are loaded before the
+        // first product and the 15 results stored after the last, so that the loads of one
+        // entry do not wait for the store of another.
+        {
+            int adr[15];
+            double wv[15], uv[15], pv[15];
 #pragma unroll
-        for (int t = 0; t < 15; t++) {
-            const int a = pa[t], b = pb[t];
-            const int sb = (int)((r + b) & 15);
-            double& w = win(sm, (int)((r + a) & 15), sb);
-            w -= sm.U[a] * win(sm, s0, sb);
+            for (int t = 0; t < 15; t++) {
+                const int ra = (int)((r + pa[t]) & 15), sb = (int)((r + pb[t]) & 15);
+                adr[t] = ra * 16 + ((sb + ra) & 15);
+                wv[t] = sm.Wf[adr[t]];
+                pv[t] = sm.Wf[s0 * 16 + ((sb + s0) & 15)];
+                uv[t] = sm.U[pa[t]];
+            }
+#pragma unroll
+            for (int t = 0; t < 15; t++) wv[t] -= uv[t] * pv[t];
+#pragma unroll
+            for (int t = 0; t < 15; t++) sm.Wf[adr[t]] = wv[t];
         }
         // the column r + 16 enters in the slot of column r (row r's entries are no longer read)
         cp_async_wait_att<kColAhead - 1>();
@@ -363,16 +374,30 @@ __global__ void __launch_bounds__(32 * kSolveSegWarps) k_att_solve(int n_seg, co
     for (int k = 0; k < 16; k++)
         if (sub == 0) sm.xs[k] = 0.0;
     __syncwarp();
+    // the row's V entries and y are loaded one row ahead (they do not depend on the x chain)
+    double u_lo = 0.0, u_hi = 0.0, y_r = 0.0;
+    if (n - 1 >= 0) {
+        const double* ur = urow + (base + n - 1) * 16;
+        u_lo = ur[sub];
+        u_hi = ur[sub + 8];
+        y_r = yv[base + n - 1];
+    }
     for (int64_t kk = 0; kk < n_max; kk++) {
         const int64_t r = n - 1 - kk;
         const bool live = r >= 0;
-        const double* ur = urow + (base + (live ? r : 0)) * 16;
-        const double p_lo = (live && sub >= 1) ? ur[sub] * sm.xs[(r + sub) & 15] : 0.0;
-        const double p_hi = live ? ur[sub + 8] * sm.xs[(r + sub + 8) & 15] : 0.0;
+        const double c_lo = u_lo, c_hi = u_hi, c_y = y_r;
+        if (r - 1 >= 0) {
+            const double* un = urow + (base + r - 1) * 16;
+            u_lo = un[sub];
+            u_hi = un[sub + 8];
+            y_r = yv[base + r - 1];
+        }
+        const double p_lo = (live && sub >= 1) ? c_lo * sm.xs[(r + sub) & 15] : 0.0;
+        const double p_hi = live ? c_hi * sm.xs[(r + sub + 8) & 15] : 0.0;
         double part = p_lo + p_hi;
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, kSegLanes);
-        const double xr = live ? yv[base + r] - part : 0.0;
+        const double xr = live ? c_y - part : 0.0;
         __syncwarp(gmask);
         if (live && sub == 0) {
             x[base + r] = xr;
