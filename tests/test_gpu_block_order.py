@@ -17,6 +17,14 @@ pytestmark = pytest.mark.gpu
 UAS = synth.UAS
 TOL_SRC = 0.5 * UAS
 ORDERS = {1: "SAC", 2: "[SAC]"}
+# Largest attitude difference allowed after two iterations, per order.  Under the Jacobi order
+# A reads the residuals from before the source update, and a one-ulp change of the starting
+# right ascensions moves the oracle's own attitude after two iterations by up to 0.55 uas
+# (RMS 0.002 uas, at a handful of weakly determined knots); under SAC by 0.05 uas.  The
+# attitude is compared at three times the larger sensitivity (and the Jacobi order also at
+# 0.01 uas RMS, five times its RMS sensitivity); the sources keep 0.5 uas.
+TOL_ATT = {1: 0.5 * UAS, 2: 1.7 * UAS}
+TOL_ATT_RMS = 0.01 * UAS
 
 
 @pytest.fixture(scope="module")
@@ -33,10 +41,10 @@ def data():
     return synth.simulate(synth.config("small1yr", n_src=3000, seed=21))
 
 
-def _attitude_angle_diff(P, a1, a2, t_ns):
+def _attitude_angles(P, a1, a2, t_ns):
     q1 = OM.attitude(P, a1, t_ns)[0]
     q2 = OM.attitude(P, a2, t_ns)[0]
-    return np.max(np.abs(OQ.diffrot(q1, q2)))
+    return np.abs(OQ.diffrot(q1, q2))
 
 
 @pytest.mark.parametrize("order", [1, 2])
@@ -56,7 +64,10 @@ def test_two_iterations_match_oracle(lib, data, order):
         assert np.allclose(it[k]["frame"], hist[k].frame, atol=1e-3 * UAS)
     e = OG.source_errors(g.sources(), state.src)
     assert np.max(np.abs(e)) < TOL_SRC, f"max source diff {np.max(np.abs(e)) / UAS:.3e} uas"
-    assert _attitude_angle_diff(P, g.attitude(), state.att, data.t_ns) < TOL_SRC
+    ang = _attitude_angles(P, g.attitude(), state.att, data.t_ns)
+    print("attitude difference: max %.3g uas, RMS %.3g uas" % (ang.max() / UAS, np.sqrt(np.mean(ang ** 2)) / UAS))
+    assert ang.max() < TOL_ATT[order]
+    assert np.sqrt(np.mean(ang ** 2)) < TOL_ATT_RMS
     assert np.max(np.abs(g.calibration() - state.cal)) < 1e-3 * UAS
     g.close()
 
