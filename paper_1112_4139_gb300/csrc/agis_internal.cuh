@@ -347,10 +347,11 @@ __device__ __forceinline__ void quat2mat_h(const double* q, double m[9]) {
 }
 
 // atan2(y, x) for a direction within 0.02 rad of the x axis by the Taylor series of arctan
-// (the remainder after the t^9 term is below 2e-20 rad); atan2 elsewhere.
+// (the remainder after the t^9 term is below 2e-20 rad; t = y / x by the Newton reciprocal
+// of x > 0, within an ulp of the quotient); atan2 elsewhere.
 __device__ __forceinline__ double atan2_small(double y, double x) {
     if (x > 0.0 && fabs(y) <= 0.02 * x) {
-        const double t = y / x, t2 = t * t;
+        const double t = y * rcp_pos(x), t2 = t * t;
         return t * (1.0 + t2 * (-1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (-1.0 / 7.0 + t2 * (1.0 / 9.0)))));
     }
     return atan2(y, x);
@@ -477,7 +478,7 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
     double ub[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) ub[i] = S.r[i] + tau * (S.p[i] * S.pma + S.q[i] * S.pmd) - S.par * b[i];
-    const double inb = 1.0 / sqrt(dot3(ub, ub));
+    const double inb = rsqrt(dot3(ub, ub));
     ub[0] *= inb; ub[1] *= inb; ub[2] *= inb;
     const double u[3] = {ub[0] + vc[0], ub[1] + vc[1], ub[2] + vc[2]};
     // attitude
@@ -572,7 +573,7 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
     const double ms[3] = {-sphi, cphi, 0.0};
     const double nsv[3] = {-szeta * cphi, -szeta * sphi, czeta};
     // back to the ICRS: x_C = R' x_S with R = Am / |s|^2
-    const double ins2 = 1.0 / (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+    const double ins2 = rcp_pos(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
     const double* e = (kind == 0) ? ms : nsv;
     const double ec[3] = {(Am[0] * e[0] + Am[3] * e[1] + Am[6] * e[2]) * ins2,
                           (Am[1] * e[0] + Am[4] * e[1] + Am[7] * e[2]) * ins2,
@@ -581,7 +582,7 @@ __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_
     const double ubv = dot3(ub, vc);
     const double eub = dot3(ec, ub);
     const double dpar[3] = {-(b[0] - S.r[0] * rb), -(b[1] - S.r[1] * rb), -(b[2] - S.r[2] * rb)};
-    const double secz = 1.0 / czeta;
+    const double secz = rcp_pos(czeta);
     const double sc = (kind == 0) ? secz : 1.0;
     const double Ap = ((1.0 - ubv) * dot3(ec, S.p) - eub * dot3(vc, S.p)) * sc;
     const double Aq = ((1.0 - ubv) * dot3(ec, S.q) - eub * dot3(vc, S.q)) * sc;

@@ -194,12 +194,16 @@ __device__ __forceinline__ RoundIn round_in(const double* s2c, double y, double 
     return r;
 }
 
-// Sums of one class over its contiguous range [lo, hi) of the source's rows (AL rows come
-// first), with the weights of class_w; the last round (store) keeps w in the scratch row for
-// the hand-over records.
+// Lane partial sums of one class over its contiguous range [lo, hi) of the source's rows (AL
+// rows come first), with the weights of class_w, written to column `lane` of the warp's
+// reduction buffer red[21][kRedStride] (15 AA, 5 Ah, hh); the last round (store) keeps w in
+// the scratch row for the hand-over records.
+constexpr int kRedVals = 42;      // both classes
+constexpr int kRedStride = 33;    // doubles per value row (odd: the column sums read distinct banks)
 __device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lane, int mode, double rx,
-                                            const double* dp, double inv_sd, int wfn, bool store, double* AA,
-                                            double* Ah, double& hh, int& nout) {
+                                            const double* dp, double inv_sd, int wfn, bool store, double* red,
+                                            int& nout) {
+    double AA[15], Ah[5];
 #pragma unroll
     for (int i = 0; i < 15; i++) AA[i] = 0.0;
 #pragma unroll
@@ -223,27 +227,34 @@ __device__ __forceinline__ void pass_class1(double* scr, int lo, int hi, int lan
         hs += w * h * h;
     }
 #pragma unroll
-    for (int i = 0; i < 15; i++) AA[i] = warp_sum(AA[i]);
+    for (int i = 0; i < 15; i++) red[i * kRedStride + lane] = AA[i];
 #pragma unroll
-    for (int i = 0; i < 5; i++) Ah[i] = warp_sum(Ah[i]);
-    hh = warp_sum(hs);
+    for (int i = 0; i < 5; i++) red[(15 + i) * kRedStride + lane] = Ah[i];
+    red[20 * kRedStride + lane] = hs;
     nout = warp_sum_int(cnt);
 }
 
-// both classes; the sums (identical in every lane after the butterflies) go to the warp's
-// shared-memory slot so that they do not occupy registers during the 5x5 algebra
+// both classes: the 42 lane partials go to the warp's reduction buffer, and lane v adds the
+// 32 partials of value v in lane order (31 additions per value instead of 5 per value in every
+// lane for butterflies); the sums go to the warp's shared-memory slot S, so that they do not
+// occupy registers during the 5x5 algebra
 __device__ __forceinline__ void pass_class(double* scr, int n, int nal, int lane, int mode, const RoundIn& ri,
-                                           const double* dp, int wfn, bool store, ClassSums& S, int& nout) {
+                                           const double* dp, int wfn, bool store, ClassSums& S, int& nout,
+                                           double* red) {
     int nc[2];
-    for (int c = 0; c < 2; c++) {
-        double AA[15], Ah[5], hh;
-        pass_class1(scr, c ? nal : 0, c ? n : nal, lane, mode, ri.rx[c], dp, ri.isd[c], wfn, store, AA, Ah, hh,
-                    nc[c]);
-        if (lane == 0) {
-            for (int i = 0; i < 15; i++) S.AA[c][i] = AA[i];
-            for (int i = 0; i < 5; i++) S.Ah[c][i] = Ah[i];
-            S.hh[c] = hh;
-        }
+    for (int c = 0; c < 2; c++)
+        pass_class1(scr, c ? nal : 0, c ? n : nal, lane, mode, ri.rx[c], dp, ri.isd[c], wfn, store,
+                    red + c * 21 * kRedStride, nc[c]);
+    __syncwarp();
+    for (int v = lane; v < kRedVals; v += kWarp) {
+        const double* col = red + v * kRedStride;
+        double t = col[0];
+#pragma unroll
+        for (int k = 1; k < kWarp; k++) t += col[k];
+        const int c = v / 21, i = v % 21;
+        if (i < 15) S.AA[c][i] = t;
+        else if (i < 20) S.Ah[c][i - 15] = t;
+        else S.hh[c] = t;
     }
     __syncwarp();
     nout = nc[0] + nc[1];
@@ -284,10 +295,10 @@ __global__ void __launch_bounds__(256) k_obs_forward(DevGeo G, AttNoise an, int6
         ObsOut ob;
         observe<1>(G, S, t, m, muv, att, cal, ob);
         const double sg = (double)sigma[o];
-        double s2 = sg * sg, x = ob.R / sg;
+        double s2 = sg * sg, x = ob.R * rcp_pos(sg);
         if (an.eps2) {
             s2 = s2 + an.eps2[an_index(an, t, m)];
-            x = ob.R / sqrt(s2);
+            x = ob.R * rsqrt(s2);
         }
         double* e = scr + (size_t)o * kScr;
         e[0] = ob.R;
@@ -399,10 +410,12 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 1) k_source_solve(
     int* work_counter) {
     __shared__ int hist_all[kSolveWarps * 256];
     __shared__ ClassSums sums_all[kSolveWarps][kWarp];
+    __shared__ double red_all[kSolveWarps][kRedVals * kRedStride];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int* hist = hist_all + wib * 256;
     ClassSums* sums = sums_all[wib];
+    double* red = red_all[wib];
     const int rounds = st.robust ? st.n_rounds + 1 : 1;
     for (;;) {
         int base = 0;
@@ -486,7 +499,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps, 1) k_source_solve(
                 const RoundIn ri = round_in(s2c, yk, vsk);
                 double* scr = scratch + (size_t)o0 * kScr;
                 int no = 0;
-                pass_class(scr, n, nal, lane, mode, ri, dk, st.weight_fn, rnd == rounds - 1, sums[k], no);
+                pass_class(scr, n, nal, lane, mode, ri, dk, st.weight_fn, rnd == rounds - 1, sums[k], no, red);
                 if (lane == k) nout = no;
             }
             __syncwarp();
