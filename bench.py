@@ -90,7 +90,7 @@ def parse():
                     help="with --convergence: also the Gauss-Seidel and Jacobi block orders (Sect. 4.6), mixed form")
     ap.add_argument("--asi-lambda-max", type=float, default=0.9, help="ASI: clamp of the lambda estimate")
     ap.add_argument("--attnoise-s", type=float, default=0.0,
-                    help="estimate the excess attitude noise on buckets of this many seconds (FP64 form, "
+                    help="estimate the excess attitude noise on buckets of this many seconds (either form, "
                          "--single-form; 0: off)")
     return ap.parse_args()
 
@@ -716,8 +716,8 @@ def main():
     head = args.precision
     other = "mixed" if head == "fp64" else "fp64"
     an_ns = int(round(args.attnoise_s * 1e9))
-    if an_ns > 0 and (head != "fp64" or not args.single_form):
-        raise SystemExit("--attnoise-s needs --precision fp64 --single-form")
+    if an_ns > 0 and not args.single_form:
+        raise SystemExit("--attnoise-s needs --single-form")
     if args.cal_generic and not (args.single_form and head == "fp64"):
         raise SystemExit("--cal-generic needs --precision fp64 --single-form (the full calibration is FP64 only)")
     calc = agis.calibration_config(ds.geometry)

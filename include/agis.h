@@ -381,8 +381,11 @@ int agis_asi_estimate(const double* d_prev, const double* d_cur, int32_t n_src, 
  *   and the next attitude update weighs observation l with w(R_l / sqrt(v)) / v,
  *             v = sigma_l^2 + eps_a^2(t_l) + eps_i^2 (Eqs. W, wl) in place of the weights of
  *             the source update; the calibration update keeps the latter.
- * bucket_ns > 0 switches the noise on (eps_a^2 = 0), 0 switches it off.  FP64 form only
- * (precision 0), block orders S[AC] and SAC, not together with ASI or the learned proposal.
+ * bucket_ns > 0 switches the noise on (eps_a^2 = 0), 0 switches it off.  Both forms: the mixed
+ * form (precision 1) forms x_l and the attitude weights from its float-pair residuals in FP64,
+ * hands the attitude update the pairs (W_l, W_l R_l) in FP32, and keeps sigma~_l as the FP32
+ * sigma of its observation records (its next source update after this call starts with a full
+ * FP64 evaluation).  Block orders S[AC] and SAC, not together with ASI or the learned proposal.
  * Errors: AGIS_E_INVALID (bucket_ns < 0, one of those combinations, an observation before
  * knot0_ns, more than 2^30 / 3 buckets), AGIS_E_OOM, AGIS_E_CUDA.  Device memory: 20 bytes
  * per observation and 48 bytes per bucket, owned by the context (and 12 bytes per

@@ -79,6 +79,12 @@ void launch_an_keys(int64_t n, const int64_t* t, const uint32_t* meta, const Att
 void launch_an_estimate(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
                         const int64_t* off, const ObsRec* rec, const float* sigma, const int32_t* obs_src,
                         const double* eps2_src, int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s);
+void launch_an_estimate_mix(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
+                            const int64_t* off, const int64_t* t_ns, const uint32_t* meta, const float2* mr,
+                            const float* sigma, const int32_t* obs_src, const double* eps2_src, int weight_fn,
+                            uint64_t* xkey, float2* ac_att, cudaStream_t s);
+void launch_an_sigma_mix(int64_t n, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+                         MixS* ms, cudaStream_t s);
 }  // namespace agis
 
 using namespace agis;
@@ -528,11 +534,13 @@ void s_done(agis_ctx* c, bool refresh) {
 
 // S block in two parts: the observation pass (timed separately) and the per-source solves
 void enqueue_s_pass(agis_ctx* c, bool refresh) {
-    if (c->mixed)
+    if (c->mixed) {
         launch_mix_pass(c->G, refresh, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src,
                         c->att, c->cal, c->mo, c->sgeo, c->d_att, c->d_cal, c->n_coef, c->n_cal, c->sh,
                         c->stream);
-    else
+        // excess attitude noise: sigma~ of the previous estimate into the records (Eq. W)
+        if (c->an.eps2) launch_an_sigma_mix(c->n_obs, c->an, c->t_ns, c->meta, c->sigma, c->mo.s, c->stream);
+    } else
         launch_obs_pass(c->G, c->an, c->t_ns, c->meta, c->sigma, c->mu, c->obs_src, c->n_obs, c->n_src, c->src, c->att,
                         c->cal, c->rec, c->sgeo, c->scratch, c->skey, c->sh, c->stream);
 }
@@ -544,7 +552,11 @@ void enqueue_s_solve(agis_ctx* c) {
         launch_source_solve(c->st, c->meta, c->src_off, c->src_nal, c->src_order, c->n_src, c->so, c->rec, c->scratch,
                             c->skey, c->work, c->n_sblocks, c->sh, c->stream);
     // excess attitude noise from the residuals of this source update, and the attitude weights
-    if (c->an.eps2)
+    if (c->an.eps2 && c->mixed)
+        launch_an_estimate_mix(c->n_obs, c->an, c->an_max_run, c->an_eps2, c->an_perm, c->an_off, c->t_ns, c->meta,
+                               c->mo.r, c->sigma, c->obs_src, c->so.eps2, c->st.weight_fn, c->an_x,
+                               reinterpret_cast<float2*>(c->an_w), c->stream);
+    else if (c->an.eps2)
         launch_an_estimate(c->n_obs, c->an, c->an_max_run, c->an_eps2, c->an_perm, c->an_off, c->rec, c->sigma,
                            c->obs_src, c->so.eps2, c->st.weight_fn, c->an_x, c->an_w, c->stream);
     launch_src_stats(c->n_src, c->so.chi2, c->so.q, c->so.nu, c->so.nout, c->so.rankdef, c->so.d, c->sstats,
@@ -577,10 +589,13 @@ void enqueue_asi(agis_ctx* c) {
         launch_prop_rec(c->n_src, c->src_off, c->scratch, c->rec, c->prop_corr, c->stream);
 }
 void enqueue_a(agis_ctx* c) {
-    if (c->mixed)
-        launch_mix_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, c->mo,
+    if (c->mixed) {
+        // with the excess attitude noise the attitude update reads its own (W, W R) pairs
+        MixObs mo = c->mo;
+        if (c->an.eps2) mo.ac = reinterpret_cast<float2*>(c->an_w);
+        launch_mix_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv, mo,
                              c->att, c->blk, c->sh, c->stream);
-    else
+    } else
         launch_att_accum(c->G, c->st.lambda2, c->st.rhs_norm_term, c->perm_t, c->ivl_off, c->n_iv,
                          c->rec, c->an.eps2 ? c->an_w : nullptr, c->att, c->blk, c->sh, c->stream);
     launch_att_solve(c->n_seg, c->max_seg_knots, c->n_coef, c->n_rows, c->seg_row, c->seg_l, c->seg_n, c->seg_u, c->blk, c->bandc,
@@ -1503,7 +1518,6 @@ int agis_set_attnoise(agis_ctx* c, int64_t bucket_ns) {
     if (!c) return AGIS_E_INVALID;
     if (bucket_ns < 0) return fail(c, AGIS_E_INVALID, "bucket_ns below 0");
     if (bucket_ns > 0) {
-        if (c->mixed) return fail(c, AGIS_E_INVALID, "the excess attitude noise needs the FP64 form (precision 0)");
         if (c->cfg.block_order == 2)
             return fail(c, AGIS_E_INVALID, "the excess attitude noise needs block order S[AC] or SAC");
         if (c->asi_stride > 0 || c->prop_every > 0)
@@ -1524,6 +1538,9 @@ int agis_set_attnoise(agis_ctx* c, int64_t bucket_ns) {
     c->an = AttNoise{};
     c->an_bucket_ns = 0;
     c->an_max_run = 0;
+    // mixed form: the records' sigma may hold sigma~; the next source update starts with a
+    // full evaluation, which rewrites it
+    c->mix_stale = true;
     if (bucket_ns == 0 || c->n_obs == 0) return AGIS_OK;
     const int64_t n = c->n_obs;
     cudaStream_t s = c->stream;

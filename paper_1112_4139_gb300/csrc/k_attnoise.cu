@@ -1,4 +1,4 @@
-// k_attnoise.cu -- excess attitude noise (Sect. 5.2.5, Eqs. excess, W, wl, e09), FP64 form.
+// k_attnoise.cu -- excess attitude noise (Sect. 5.2.5, Eqs. excess, W, wl, e09), both forms.
 //
 // The excess noise of observation l is split into a source part and an attitude part,
 // eps_l^2 = eps_i^2 + eps_a^2(t_l), with one attitude function per component (AL, AC in the
@@ -18,6 +18,11 @@
 // timing or launch shape: one warp per run of up to kWarpRun keys (no block barriers; a pass
 // whose chosen digit holds a single key ends the select, about 4 passes instead of 8 on
 // continuous data), one block per longer run.
+//
+// Mixed form: x_l and the attitude weights come from the float-pair residuals (R = hi + lo in
+// FP64, as exact as the FP64 form's to about 48 bits); the attitude update reads the pairs
+// (W_l, W_l R_l) in FP32 like its other inputs, and the source update reads sigma~_l as the
+// FP32 sigma of the observation records (k_an_sigma_mix, after every observation pass).
 #include "agis_internal.cuh"
 
 namespace agis {
@@ -311,6 +316,50 @@ void launch_an_keys(int64_t n, const int64_t* t, const uint32_t* meta, const Att
 // eps_a^2 from the residuals of the source update just made, then the attitude weights.
 // an.eps2 and eps2 are the same array (written here); max_run: the longest run (the block
 // kernel runs only when some run is longer than kWarpRun).
+// mixed form: x_l from the float-pair residual R = hi + lo
+__global__ void k_an_values_mix(int64_t n, const uint32_t* __restrict__ perm, const float2* __restrict__ mr,
+                                const float* __restrict__ sigma, const int32_t* __restrict__ obs_src,
+                                const double* __restrict__ eps2_src, uint64_t* __restrict__ xkey) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = perm[p];
+        const float2 r = mr[o];
+        const double R = (double)r.x + (double)r.y;
+        const double s = (double)sigma[o];
+        const double x = __dadd_rn(__dadd_rn(__dmul_rn(R, R), -__dmul_rn(s, s)), -eps2_src[obs_src[o]]);
+        xkey[p] = dkey(x);
+    }
+}
+
+// mixed form: the attitude update's pairs (W_l, W_l R_l), W_l = w(R_l / sqrt(v)) / v
+__global__ void k_an_weights_mix(int64_t n, AttNoise an, const int64_t* __restrict__ t_ns,
+                                 const uint32_t* __restrict__ meta, const float2* __restrict__ mr,
+                                 const float* __restrict__ sigma, const int32_t* __restrict__ obs_src,
+                                 const double* __restrict__ eps2_src, int weight_fn, float2* __restrict__ ac_att) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const float2 r = mr[o];
+        const double R = (double)r.x + (double)r.y;
+        const double s = (double)sigma[o];
+        const double v = __dadd_rn(__dadd_rn(__dmul_rn(s, s), an.eps2[an_index(an, t_ns[o], meta[o])]),
+                                   eps2_src[obs_src[o]]);
+        const double W = wfun(R / sqrt(v), weight_fn) / v;
+        ac_att[o] = make_float2((float)W, (float)(W * R));
+    }
+}
+
+// mixed form: sigma~_l = sqrt(sigma_l^2 + eps_a^2(t_l)) into the observation records (sign:
+// + AL, - AC, as the records keep it); eps2 null restores sigma_l
+__global__ void k_an_sigma_mix(int64_t n, AttNoise an, const int64_t* __restrict__ t_ns,
+                               const uint32_t* __restrict__ meta, const float* __restrict__ sigma,
+                               MixS* __restrict__ ms) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = meta[o];
+        const double s = (double)sigma[o];
+        const double v = an.eps2 ? __dadd_rn(__dmul_rn(s, s), an.eps2[an_index(an, t_ns[o], m)]) : s * s;
+        const float sg = (float)sqrt(v);
+        ms[o].sig = meta_kind(m) ? -sg : sg;
+    }
+}
+
 void launch_an_estimate(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
                         const int64_t* off, const ObsRec* rec, const float* sigma, const int32_t* obs_src,
                         const double* eps2_src, int weight_fn, uint64_t* xkey, double* w_att, cudaStream_t s) {
@@ -324,6 +373,29 @@ void launch_an_estimate(int64_t n, const AttNoise& an, int64_t max_run, double* 
         k_an_select<<<blocks, kSelThreads, 0, s>>>(n_run, off, xkey, 0.68, eps2);
     }
     k_an_weights<<<an_grid(n), 256, 0, s>>>(n, an, rec, sigma, obs_src, eps2_src, weight_fn, w_att);
+}
+
+
+void launch_an_estimate_mix(int64_t n, const AttNoise& an, int64_t max_run, double* eps2, const uint32_t* perm,
+                            const int64_t* off, const int64_t* t_ns, const uint32_t* meta, const float2* mr,
+                            const float* sigma, const int32_t* obs_src, const double* eps2_src, int weight_fn,
+                            uint64_t* xkey, float2* ac_att, cudaStream_t s) {
+    if (n == 0 || an.n_b == 0) return;
+    k_an_values_mix<<<an_grid(n), 256, 0, s>>>(n, perm, mr, sigma, obs_src, eps2_src, xkey);
+    const int n_run = 3 * an.n_b;
+    const int wblocks = (n_run + kSelWarps - 1) / kSelWarps;
+    k_an_select_warp<<<wblocks < 152 * 16 ? wblocks : 152 * 16, 32 * kSelWarps, 0, s>>>(n_run, off, xkey, 0.68, eps2);
+    if (max_run > kWarpRun) {
+        const int blocks = n_run < 152 * 8 ? n_run : 152 * 8;
+        k_an_select<<<blocks, kSelThreads, 0, s>>>(n_run, off, xkey, 0.68, eps2);
+    }
+    k_an_weights_mix<<<an_grid(n), 256, 0, s>>>(n, an, t_ns, meta, mr, sigma, obs_src, eps2_src, weight_fn, ac_att);
+}
+
+void launch_an_sigma_mix(int64_t n, const AttNoise& an, const int64_t* t_ns, const uint32_t* meta, const float* sigma,
+                         MixS* ms, cudaStream_t s) {
+    if (n == 0) return;
+    k_an_sigma_mix<<<an_grid(n), 256, 0, s>>>(n, an, t_ns, meta, sigma, ms);
 }
 
 }  // namespace agis
