@@ -1068,6 +1068,24 @@ int agis_init(const agis_geometry* geo, const agis_config* cfg, const agis_obs* 
         (rc = dalloc(c, &c->sstats, 16)) || (rc = dalloc(c, &c->sstat_part, 512 * 10)))
         return bail(rc);
     c->so.src = c->src;
+    // the orbital longitude tabulated over the knot range with one step of margin either
+    // side (observations outside take sincospi)
+    {
+        const int64_t step = (int64_t)1 << kOrbShift;
+        const int64_t span = (int64_t)std::max(n_coef - 3, 1) * geo->knot_dt_ns;
+        const int32_t n_tab = (int32_t)((span + 2 * step) / step + 1);
+        std::vector<double> tab(2 * (size_t)n_tab);
+        G.orb_t0 = geo->knot0_ns - step;
+        G.orb_n = n_tab;
+        fill_orbit_table(G, G.orb_t0, n_tab, tab.data());
+        double* dtab = nullptr;
+        if ((rc = dalloc(c, &dtab, tab.size()))) return bail(rc);
+        if (cuda_check(c, cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s),
+                       "orbit table") != AGIS_OK ||
+            cuda_check(c, cudaStreamSynchronize(s), "orbit table (sync)") != AGIS_OK)
+            return bail(AGIS_E_CUDA);
+        G.orb_tab = dtab;
+    }
     if ((rc = dalloc(c, &c->hist, 20 * (size_t)n_src))) return bail(rc);
     cudaMemsetAsync(c->hist, 0, sizeof(double) * 20 * (size_t)n_src, s);
     // ---- segments and band storage

@@ -51,7 +51,14 @@ struct DevGeo {
     double inv_knot_dt;
     int32_t n_coef;
     CalGen cg;
+    // orbital longitude tabulated every 2^kOrbShift ns from orb_t0: (sin L, cos L) pairs, and
+    // the longitude rate per ns (null table: sincospi of the linear longitude)
+    const double* orb_tab;
+    int64_t orb_t0;
+    int32_t orb_n;
+    double orb_rad_per_ns;
 };
+constexpr int kOrbShift = 42;   // 4398 s: 8.8e-4 rad of orbital longitude per table step
 
 inline void fill_devgeo(const agis_geometry* geo, int32_t n_coef, DevGeo& G) {
     const double pi = 3.141592653589793;
@@ -83,6 +90,19 @@ inline void fill_devgeo(const agis_geometry* geo, int32_t n_coef, DevGeo& G) {
     G.knot_dt_ns = geo->knot_dt_ns;
     G.inv_knot_dt = 1.0 / (double)geo->knot_dt_ns;
     G.n_coef = n_coef;
+    G.orb_rad_per_ns = G.orb_rate * 1e-9;
+}
+
+// (sin L, cos L) of the tabulated longitude L(t_j) = L0 + 2 pi (t_j / 1e9) / year at
+// t_j = t0 + j 2^kOrbShift, j = 0 .. n-1 (host, at set-up)
+inline void fill_orbit_table(const DevGeo& G, int64_t t0, int32_t n, double* tab) {
+    const double pi = 3.141592653589793;
+    for (int32_t j = 0; j < n; j++) {
+        const int64_t t = t0 + ((int64_t)j << kOrbShift);
+        const double x = G.orb_L0_pi + 2.0 * ((double)t * 1e-9) * G.inv_year_s;
+        tab[2 * j] = std::sin(pi * x);
+        tab[2 * j + 1] = std::cos(pi * x);
+    }
 }
 
 // Hand-over record written by the S pass and read (gathered) by the A and C passes.
@@ -357,6 +377,28 @@ __device__ __forceinline__ double atan2_small(double y, double x) {
     return atan2(y, x);
 }
 
+// sin and cos of the orbital longitude L(t) = L0 + 2 pi (t / 1e9) / year: from the table point
+// at or before t by the angle-addition formulas, with sin and cos of the offset d < 8.8e-4 rad
+// by their Taylor series to d^5 and d^6 (remainders below 1e-25); sincospi of L / pi where
+// there is no table or t lies outside it.
+__device__ __forceinline__ void orbit_sincos(const DevGeo& G, int64_t t, double& sL, double& cL) {
+    if (G.orb_tab) {
+        const int64_t rel = t - G.orb_t0;
+        const int64_t j = rel >> kOrbShift;
+        if (rel >= 0 && j < G.orb_n) {
+            const double d = (double)(rel - (j << kOrbShift)) * G.orb_rad_per_ns;
+            const double d2 = d * d;
+            const double sd = d * (1.0 + d2 * (-1.0 / 6.0 + d2 * (1.0 / 120.0)));
+            const double cd = 1.0 + d2 * (-0.5 + d2 * (1.0 / 24.0 + d2 * (-1.0 / 720.0)));
+            const double s0 = G.orb_tab[2 * j], c0 = G.orb_tab[2 * j + 1];
+            sL = fma(s0, cd, c0 * sd);
+            cL = fma(c0, cd, -(s0 * sd));
+            return;
+        }
+    }
+    sincospi(G.orb_L0_pi + 2.0 * ((double)t * 1e-9) * G.inv_year_s, &sL, &cL);
+}
+
 // Per-source geometry: normal triad (Eq. normal-triad) and the parameters.
 struct SrcGeo {
     double p[3], q[3], r[3];
@@ -467,9 +509,9 @@ template <int kPartials>
 __device__ __forceinline__ void observe(const DevGeo& G, const SrcGeo& S, int64_t t, uint32_t meta, double mu,
                                         const double* __restrict__ att, const double* __restrict__ cal,
                                         ObsOut& o) {
-    // ephemeris: circular orbit, ICRS components (AU, AU/s in units of c); L = pi x
+    // ephemeris: circular orbit, ICRS components (AU, AU/s in units of c)
     double sL, cL;
-    sincospi(G.orb_L0_pi + 2.0 * ((double)t * 1e-9) * G.inv_year_s, &sL, &cL);
+    orbit_sincos(G, t, sL, cL);
     const double b[3] = {cL, G.cos_obl * sL, G.sin_obl * sL};
     const double vc[3] = {-G.vk * sL, G.vk * G.cos_obl * cL, G.vk * G.sin_obl * cL};
     // Roemer delay and proper-motion time

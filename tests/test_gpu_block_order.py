@@ -17,14 +17,14 @@ pytestmark = pytest.mark.gpu
 UAS = synth.UAS
 TOL_SRC = 0.5 * UAS
 ORDERS = {1: "SAC", 2: "[SAC]"}
-# Largest attitude difference allowed after two iterations, per order.  Under the Jacobi order
-# A reads the residuals from before the source update, and a one-ulp change of the starting
-# right ascensions moves the oracle's own attitude after two iterations by up to 0.55 uas
-# (RMS 0.002 uas, at a handful of weakly determined knots); under SAC by 0.05 uas.  The
-# attitude is compared at three times the larger sensitivity (and the Jacobi order also at
-# 0.01 uas RMS, five times its RMS sensitivity); the sources keep 0.5 uas.
-TOL_ATT = {1: 0.5 * UAS, 2: 1.7 * UAS}
-TOL_ATT_RMS = 0.01 * UAS
+# Attitude difference allowed after two iterations, per order: three times the oracle's own
+# sensitivity to rounding, measured on this set as the change of its attitude after two
+# iterations when every starting source parameter and attitude coefficient moves by one ulp
+# in a random direction: 0.20 uas at most (RMS 0.0007 uas) under SAC, 0.52 uas (RMS 0.0019
+# uas) under Jacobi, where A reads the residuals from before the source update.  A handful of
+# weakly determined knots carry these maxima.
+TOL_ATT = {1: 0.6 * UAS, 2: 1.6 * UAS}
+TOL_ATT_RMS = {1: 0.0025 * UAS, 2: 0.006 * UAS}
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +67,7 @@ def test_two_iterations_match_oracle(lib, data, order):
     ang = _attitude_angles(P, g.attitude(), state.att, data.t_ns)
     print("attitude difference: max %.3g uas, RMS %.3g uas" % (ang.max() / UAS, np.sqrt(np.mean(ang ** 2)) / UAS))
     assert ang.max() < TOL_ATT[order]
-    assert np.sqrt(np.mean(ang ** 2)) < TOL_ATT_RMS
+    assert np.sqrt(np.mean(ang ** 2)) < TOL_ATT_RMS[order]
     assert np.max(np.abs(g.calibration() - state.cal)) < 1e-3 * UAS
     g.close()
 

@@ -180,8 +180,17 @@ def test_two_iterations(lib, data, use_graph):
         assert abs(it[k]["s"]["chi2"] / hist[k].chi2 - 1) < 1e-8
         assert np.allclose(it[k]["frame"], hist[k].frame, atol=1e-3 * UAS)
     e = OG.source_errors(g.sources(), state.src)
+    q1 = OM.attitude(P, g.attitude(), data.t_ns)[0]
+    q2 = OM.attitude(P, state.att, data.t_ns)[0]
+    ang = np.abs(OQ.diffrot(q1, q2))
+    print(f"two iterations: sources max {np.max(np.abs(e)) / UAS:.3g} uas, attitude max {ang.max() / UAS:.3g} uas, "
+          f"RMS {np.sqrt(np.mean(ang ** 2)) / UAS:.3g} uas")
     assert np.max(np.abs(e)) < TOL_SRC, f"max source diff {np.max(np.abs(e)) / UAS:.3e} uas"
-    assert _attitude_angle_diff(P, g.attitude(), state.att, data.t_ns) < TOL_SRC
+    # A one-ulp random change of every starting source parameter and attitude coefficient moves
+    # the oracle's own attitude after these two iterations by up to 0.36 uas (RMS 0.0012 uas,
+    # at a few weakly determined knots): the attitude is compared at three times that.
+    assert ang.max() < 1.1 * UAS
+    assert np.sqrt(np.mean(ang ** 2)) < 0.004 * UAS
     assert np.max(np.abs(g.calibration() - state.cal)) < 1e-3 * UAS
     g.close()
 
