@@ -314,8 +314,10 @@ class OracleSampler:
         thr_c1 = len(args_c) / sum(r[1] for r in res_c)
         t_iter = ds.n_obs / thr_s + len(self.segs) / thr_a + self.days / thr_c
         t_iter1 = ds.n_obs / thr_s1 + len(self.segs) / thr_a1 + self.days / thr_c1
-        sample = (f"S block on {50 * n_tasks} sources ({n_s} obs, {n_tasks} runs of 50 consecutive sources from "
-                  f"random places), A block on {len(res_a)} of {len(self.segs)} segments "
+        distinct = min(n_tasks, self.starts.size)
+        again = f", {n_tasks - distinct} of them again (the set has {self.starts.size})" if n_tasks > distinct else ""
+        sample = (f"S block on {n_s} obs of {n_tasks} runs of 50 consecutive sources from random places{again}, "
+                  f"A block on {len(res_a)} of {len(self.segs)} segments "
                   f"(~{int(np.mean([r[0] for r in res_a]))} obs each), C block on {len(res_c)} of {self.days} "
                   f"intervals, in {self.workers} worker processes; per-iteration time extrapolated to {ds.n_obs} obs "
                   f"= {t_iter:.1f} s ({t_iter1:.1f} s on one core); sample selection {self.t_select:.1f} s, not counted")
